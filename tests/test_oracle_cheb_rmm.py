@@ -1,0 +1,124 @@
+"""Pins for ChebFSI (Alg. 3), RMM-DIIS (Alg. 4) and the hybrid switch (Eq. switchtau)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import (laplacian_kron, laplacian_kron_eigs, diagonal_matrix, ci_matrix, random_block,
+                 principal_submatrix, pad_rows)
+
+
+def cheb_scalar(m, t):
+    """T_m(t) = cos(m arccos t) on [-1, 1] and cosh(m arccosh |t|) (with sign (-1)^m for t < -1)."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.empty_like(t)
+    inside = np.abs(t) <= 1
+    out[inside] = np.cos(m * np.arccos(t[inside]))
+    o = ~inside
+    out[o] = np.cosh(m * np.arccosh(np.abs(t[o]))) * np.where(t[o] < 0, (-1.0) ** m, 1.0)
+    return out
+
+
+@pytest.mark.parametrize("deg", [1, 2, 5, 10, 24])
+def test_cheb_filter_diagonal_matches_scalar(deg):
+    d = np.linspace(-1.5, 9.0, 40)
+    H = diagonal_matrix(d)
+    c, e = 4.0, 3.0
+    Q = np.eye(40)[:, :40]
+    Y, prods = O.cheb_filter(H, Q, O.sym_upper_matmul(H, Q), deg, c, e)
+    assert prods == deg - 1
+    np.testing.assert_allclose(np.diag(Y), cheb_scalar(deg, (d - c) / e), rtol=1e-12, atol=1e-12)
+
+
+def test_cheb_filter_locked_columns_untouched():
+    d = np.linspace(0, 5, 10)
+    H = diagonal_matrix(d)
+    Q = np.eye(10)
+    act = np.array([True] * 5 + [False] * 5)
+    Y, _ = O.cheb_filter(H, Q, O.sym_upper_matmul(H, Q), 6, 3.0, 2.0, act)
+    np.testing.assert_array_equal(Y[:, 5:], Q[:, 5:])
+
+
+def test_lambda_ub_and_chebfsi_laplacian():
+    dims = [9, 11, 13]
+    H = laplacian_kron(dims)
+    exact = laplacian_kron_eigs(dims)
+    lub, k = O.lambda_ub_estimate(H, random_block(H.n, 1, 3)[:, 0])
+    assert k == 10
+    assert exact[-1] <= lub <= exact[-1] * 1.2
+    r = O.chebfsi(H, random_block(H.n, 8, 5), 5, deg=10, tol=1e-8, v_ub=random_block(H.n, 1, 3)[:, 0])
+    assert r.converged
+    np.testing.assert_allclose(r.theta, exact[:5], rtol=1e-10)
+
+
+def test_rr2_closed_form():
+    rng = np.random.default_rng(0)
+    A0 = rng.standard_normal((30, 30)); A0 = A0 + A0.T
+    x, r = rng.standard_normal(30), rng.standard_normal(30)
+    Hx, Hr = A0 @ x, A0 @ r
+    th, g = O.rr2(x, r, Hx, Hr)
+    a11, a12, a22 = x @ Hx, x @ Hr, r @ Hr
+    b11, b12, b22 = x @ x, x @ r, r @ r
+    qa = b11 * b22 - b12 ** 2
+    qb = -(a11 * b22 + a22 * b11 - 2 * a12 * b12)
+    qc = a11 * a22 - a12 ** 2
+    root = (-qb - np.sqrt(qb * qb - 4 * qa * qc)) / (2 * qa)
+    assert abs(th - root) < 1e-10 * abs(root)
+    w = g[0] * x + g[1] * r
+    assert abs(w @ w - 1) < 1e-12
+
+
+def test_diis_two_vector_closed_form():
+    rng = np.random.default_rng(1)
+    r1, r2 = rng.standard_normal(50), rng.standard_normal(50)
+    a = O.diis_coefficients([r1, r2])
+    a_old = (r2 @ (r2 - r1)) / ((r2 - r1) @ (r2 - r1))
+    np.testing.assert_allclose(a, [a_old, 1 - a_old], rtol=1e-12)
+    assert O.diis_coefficients([r1]).tolist() == [1.0]
+
+
+def test_rmmdiis_fixed_point_and_convergence():
+    dims = [9, 10, 11]
+    H = laplacian_kron(dims)
+    lam, V = O.lowest_eigpairs(O.to_dense(H), 3)
+    r = O.rmmdiis(H, V, tol=1e-10)
+    assert r.converged and r.iterations == 0
+    X0 = V + 1e-3 * random_block(H.n, 3, 7)
+    r = O.rmmdiis(H, X0, tol=1e-9, maxiter=400, s_max=20)
+    assert r.converged
+    np.testing.assert_allclose(r.theta, lam, rtol=1e-10)
+    assert np.all(O.true_relres(H, r.theta, r.X) < 1e-8)
+
+
+def test_switch_tau_hand_value():
+    # changes: (1.0-1.1)/1.0 = -0.1, (2.0-2.2)/2.0 = -0.1 -> sqrt(0.02)/2 = 0.0707106781...
+    assert abs(O.switch_tau([1.0, 2.0], [1.1, 2.2]) - 0.07071067811865475) < 1e-15
+    assert O.switch_tau([3.0, 4.0], [3.0, 4.0]) == 0.0
+
+
+def test_hybrid_ci_vs_dense():
+    H = ci_matrix(3000, 100, 64, seed=1, storage="f64")
+    lam, _ = O.lowest_eigpairs(O.to_dense(H), 5)
+    Z0 = O.lowest_eigpairs(O.to_dense(principal_submatrix(H, 300)), 8)[1]
+    X0 = pad_rows(Z0, H.n)
+    for front, tau in [("lobpcg", 1e-7), ("block_lanczos", 1e-7)]:
+        r = O.hybrid(H, X0, 5, tol=1e-6, front=front, switch_tau_tol=tau, rmm_maxiter=400)
+        assert r.converged, front
+        np.testing.assert_allclose(r.theta, lam, rtol=1e-9)
+        assert np.all(O.true_relres(H, r.theta, r.X) < 1e-6)
+    r = O.hybrid(H, X0, 5, tol=1e-6, switch_after=3, switch_tau_tol=None, rmm_maxiter=400)
+    assert r.extra["front_iterations"] == 3 and r.extra["switch"] == "after"
+
+
+def test_planted_mistakes_are_caught():
+    """Wrong-sign recurrence and a DIIS that drops the constraint both fail their pins."""
+    d = np.linspace(-1.5, 9.0, 40)
+    t = (d - 4.0) / 3.0
+    # a recurrence with + Q instead of - Q
+    W1, W0 = t, np.ones_like(t)
+    wrong = 2 * t * W1 + W0
+    assert np.abs(wrong - cheb_scalar(2, t)).max() > 1.0
+    rng = np.random.default_rng(1)
+    r1, r2 = rng.standard_normal(50), rng.standard_normal(50)
+    a_old = (r2 @ (r2 - r1)) / ((r2 - r1) @ (r2 - r1))
+    a_wrong = (r1 @ (r2 - r1)) / ((r2 - r1) @ (r2 - r1))
+    assert abs(a_wrong - a_old) > 1e-3
