@@ -1,0 +1,325 @@
+"""Time-to-solution benchmark of the hybrid LOBPCG -> RMM-DIIS eigensolver (one JSON line).
+
+Workload (the hybrid-solver configuration): n = 2,000,000, ~400 nonzeros per full row on a
+seeded 256 x 256 block pattern, half-stored (~4e8 stored nonzeros), FP32 values; the lowest
+n_ev = 8 eigenpairs, block n_b = 16, LOBPCG front switched to batched RMM-DIIS by the tau rule
+of Eq. (switchtau), relative residual 1e-6.  The initial guess is the zero-padded lowest
+eigenvectors of the leading n/10 principal block (the smaller-model-space start of Sec. 3.1),
+computed beforehand on the GPU and excluded from the timing, as in the paper.
+
+A step is one complete solve (eig_solve) with H resident in HBM.  `e2e` repeats the metric
+through the C ABI from host buffers: eig_create (H copied in and planned), eig_solve with a
+host X0, eig_ritz copying the eigenvectors back.  `cpu_baseline` times the FP64 CPU oracle on
+a bounded sample of the same workload and scales it to a whole solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N] ...
+N > 1 runs under torchrun: every rank solves its own replica (replicas only: the solve has no
+data-parallel exchange on one node here), timing is max over ranks.
+"""
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution, lowest n_ev eigenpairs at rel. residual 1e-6; SpMM HBM GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--nnz-per-row", type=float, default=400)
+    ap.add_argument("--block-pattern", type=int, default=256)
+    ap.add_argument("--nev", type=int, default=8)
+    ap.add_argument("--nb", type=int, default=16)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--vec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def reduce_max(value, ws, device=None):
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def make_problem(args):
+    from gen import ci_matrix
+    t = time.time()
+    H = ci_matrix(args.n, args.nnz_per_row, args.block_pattern, seed=args.seed, storage=args.storage)
+    return H, time.time() - t
+
+
+def initial_guess(H, args, binding):
+    """Zero-padded lowest eigenvectors of the leading n/10 principal block, solved on the GPU."""
+    from gen import principal_submatrix, pad_rows
+    n0 = max(args.nb * 8, H.n // 10)
+    H0 = principal_submatrix(H, n0)
+    S0 = binding.Solver(H0, args.nb, args.nb)
+    rc, st = S0.solve("hybrid", vec_type=args.vec, tol=1e-4, seed=args.seed)
+    _, X0, _ = S0.ritz()
+    S0.close()
+    return pad_rows(X0, H.n)
+
+
+def cpu_baseline(H, stats, args):
+    """The FP64 oracle, timed on a bounded sample: one of its products with a 16-column block
+    (a LOBPCG iteration's SpMM) and one with an 8-column block, scaled by the iteration counts
+    of the GPU solve (the oracle's hybrid does 1 product per LOBPCG iteration and 3 per
+    RMM-DIIS iteration)."""
+    import oracle as O
+    U = O.to_scipy_upper(H)
+    rng = np.random.default_rng(0)
+    t16 = t8 = None
+    X = rng.standard_normal((H.n, args.nb))
+    t = time.time(); O.sym_upper_matmul(H, X, U); t16 = time.time() - t
+    X = rng.standard_normal((H.n, args.nev))
+    t = time.time(); O.sym_upper_matmul(H, X, U); t8 = time.time() - t
+    est_s = t16 * (1 + stats["iterations_front"]) + 3 * t8 * stats["iterations_rmm"]
+    return {"value": est_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": (f"one oracle product with a {args.nb}-column block ({t16:.2f} s) and one with an "
+                       f"{args.nev}-column block ({t8:.2f} s) on the full matrix (scipy sparse, 1 thread), "
+                       f"scaled by the GPU solve's {stats['iterations_front']} LOBPCG + "
+                       f"{stats['iterations_rmm']} RMM-DIIS iterations")}
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the FP64 CPU oracle on the same workload, each step a bounded sample
+    (one oracle LOBPCG iteration on the full matrix), scaled to a whole solve by the iteration
+    counts the oracle hybrid needs on the 1/10 principal block."""
+    if rank != 0:
+        return
+    import oracle as O
+    from gen import principal_submatrix, pad_rows
+    H, tgen = make_problem(args)
+    U = O.to_scipy_upper(H)
+    # iteration counts from a full oracle hybrid on the leading 1/10 block (not timed)
+    n0 = max(args.nb * 8, H.n // 10)
+    H0 = principal_submatrix(H, n0)
+    U0 = O.to_scipy_upper(H0)
+    n00 = max(args.nb * 4, n0 // 10)
+    Z00 = O.lobpcg(principal_submatrix(H0, n00), np.random.default_rng(1).standard_normal((n00, args.nb)),
+                   args.nb, tol=1e-4, maxiter=200).X
+    ref0 = O.hybrid(H0, pad_rows(Z00, n0), args.nev, tol=args.tol, U=U0, rmm_maxiter=300)
+    it_f, it_r = ref0.extra["front"].iterations, (ref0.extra["rmm"].iterations if ref0.extra["rmm"] else 0)
+    X = np.random.default_rng(2).standard_normal((H.n, args.nb))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.time()
+        O.lobpcg(H, X, args.nev, tol=args.tol, maxiter=1, U=U)
+        dt = time.time() - t
+        if i >= args.warmup:
+            times.append(dt)
+    t_it = statistics.median(times) / 2.0  # lobpcg(maxiter=1) = initial RR + one iteration
+    est_ms = (t_it * (1 + it_f) + 3 * t_it / 2 * it_r) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": est_ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est_ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, H),
+            "cpu_baseline": {"value": est_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": (f"median of {args.steps} oracle LOBPCG steps (maxiter=1) on the full matrix, "
+                                        f"scaled by the oracle hybrid's {it_f} LOBPCG + {it_r} RMM-DIIS iterations "
+                                        f"on the leading n/10 block")},
+            "e2e": {"value": est_ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, H):
+    return {"workload": (f"hybrid LOBPCG->RMM-DIIS, n={H.n:,}, ~{args.nnz_per_row:g} nnz/row, "
+                         f"block pattern {args.block_pattern}, half-stored nnz={H.nnz:,}, "
+                         f"{args.storage} values / {args.vec} vectors, n_ev={args.nev}, block {args.nb}, "
+                         f"tol {args.tol:g}"),
+            "n": H.n, "nnz_half": H.nnz, "n_ev": args.nev, "block": args.nb, "values": args.storage,
+            "vectors": args.vec, "l2": "inputs larger than L2 (matrix ~3.2 GB), no flush",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        barrier(ws)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2305_15552_gb300 import binding
+    lib = binding.load()
+    H, tgen = make_problem(args)
+    X0 = initial_guess(H, args, binding)
+    X0d = torch.tensor(X0, device="cuda")
+    S = binding.Solver(H, args.nev, args.nb)
+    opts = dict(vec_type=args.vec, tol=args.tol, timing=1, maxiter=500)
+    st_ = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        S.solve("hybrid", X0=X0d, **opts)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    spmm_ms = spmm_bytes = 0.0
+    spmm_calls = 0
+    stats = None
+    launches0 = lib.eig_launch_count()
+    with ClockSampler(local) as clk:
+        ev0.record(st_)
+        for _ in range(args.steps):
+            rc, stats = S.solve("hybrid", X0=X0d, **opts)
+            spmm_ms += stats["time_ms_spmm"]
+            spmm_bytes += stats["spmm_bytes"]
+            spmm_calls += stats["spmm_timed"]
+        ev1.record(st_)
+        torch.cuda.synchronize()
+    launches = lib.eig_launch_count() - launches0
+    barrier(ws)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = reduce_max(ms, ws, "cuda")
+    th, X, rel = S.ritz()
+    S.close()
+    # end to end through the C ABI from host buffers
+    e2e_ms = []
+    h2d = H.rowptr.nbytes + H.col.nbytes + H.val.nbytes + X0.nbytes
+    d2h = H.n * args.nev * 8 + 2 * args.nev * 8
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        S2 = binding.Solver(H, args.nev, args.nb)
+        S2.solve("hybrid", X0=X0, vec_type=args.vec, tol=args.tol, maxiter=500)
+        S2.ritz()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+        S2.close()
+    e2e = reduce_max(min(e2e_ms), ws, "cuda") if e2e_ms else None
+    peak, peak_kind = measured_peak()
+    spmm_avg_ms = spmm_ms / max(spmm_calls, 1)
+    achieved = (spmm_bytes / max(spmm_ms, 1e-9)) / 1e6  # GB/s
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.vec, "data": "synthetic",
+        "config": workload_config(args, H),
+        "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "symmetric SpMM (row-block pass + transpose-schedule reduce)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": spmm_bytes / max(spmm_calls, 1),
+                     "avg_launch_ms": spmm_avg_ms, "launches_per_step": spmm_calls / args.steps},
+        "solve": {"status": rc, "iterations_front": stats["iterations_front"],
+                  "iterations_rmm": stats["iterations_rmm"], "spmv_count": stats["spmv_count"],
+                  "spmm_calls": stats["spmm_calls"], "max_relres": stats["max_relres"],
+                  "switch_reason": stats["switch_reason"], "spmm_share": spmm_ms / (ms * args.steps),
+                  "theta": [float(v) for v in th]},
+        "clocks": clk.summary(),
+        "host": {"machine": platform.machine(), "cpus": os.cpu_count(), "gen_s": tgen},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(H, stats, args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
+if __name__ == "__main__":
+    main()

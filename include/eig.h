@@ -1,0 +1,250 @@
+/*
+ * eig.h -- C ABI of the GB300 (sm_103a) hybrid sparse eigensolver library (libeig.so).
+ *
+ * Computes the n_ev algebraically smallest eigenpairs of a large sparse symmetric H
+ * stored as its upper triangle (Alperen, Aktulga, Maris, Yang, "Hybrid Eigensolvers for
+ * Nuclear Configuration Interaction Calculations", arXiv 2305.15552; Sec. 2 defines the
+ * problem, Sec. 3.1 the half-stored matrices).
+ *
+ * Conventions shared by every entry point
+ *   - All sizes are in elements.  Blocks of vectors are row-major n x k arrays (row i holds
+ *     the k entries x_i1..x_ik contiguously); leading dimension = k unless stated.
+ *   - "device" pointers are CUDA global-memory pointers of the current device; "host"
+ *     pointers are ordinary CPU memory.  The library never frees caller memory and never
+ *     keeps a caller pointer after a call returns, except where a handle documents it.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued on it; calls that must read results back synchronise that stream only.
+ *   - Errors: every call returns eig_status.  EIG_EINVAL for bad arguments (nothing is
+ *     launched), EIG_ECUDA when a CUDA call failed (eig_last_cuda_error() gives the CUDA
+ *     message), EIG_ENOMEM when device allocation failed.  A failed call leaves caller
+ *     buffers in an unspecified state but never corrupts a handle.
+ *   - No CPU fallback: every arithmetic step runs in this library's CUDA kernels.
+ */
+#ifndef EIG_H_
+#define EIG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EIG_API __attribute__((visibility("default")))
+#else
+#define EIG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EIG_OK = 0,
+  EIG_EINVAL = 1,          /* invalid argument (sizes, pointers, CSR structure)            */
+  EIG_ENOMEM = 2,          /* device allocation failed                                     */
+  EIG_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed                  */
+  EIG_ENOT_CONVERGED = 4,  /* maxiter reached; eig_ritz still returns the best pairs       */
+  EIG_EBREAKDOWN = 5,      /* CholeskyQR / Rayleigh-Ritz basis numerically rank deficient  */
+  EIG_ETIMEOUT = 6,        /* a bounded device-side wait gave up                           */
+  EIG_EDUPLICATE = 7,      /* two returned eigenpairs collapsed onto the same eigenvector  */
+  EIG_EUNSUPPORTED = 8     /* valid request this build does not implement (e.g. a k > max) */
+} eig_status;
+
+typedef enum { EIG_F64 = 0, EIG_F32 = 1, EIG_BF16 = 2 } eig_dtype;
+
+typedef enum {
+  EIG_LANCZOS = 0,         /* Sec. 2.1, Eqs. (krylov)-(ritzest1)                          */
+  EIG_BLOCK_LANCZOS = 1,   /* Alg. 1                                                      */
+  EIG_LOBPCG = 2,          /* Alg. 2                                                      */
+  EIG_CHEBFILTER = 3,      /* Alg. 3 (ChebFSI)                                            */
+  EIG_RMMDIIS = 4,         /* Alg. 4, batched over eigenvectors (Sec. 4.3)                */
+  EIG_HYBRID = 5           /* Sec. 2.8 / Sec. 4: front method, then batched RMM-DIIS      */
+} eig_method;
+
+/* Upper triangle (incl. diagonal) of a symmetric n x n matrix, CSR.
+ * rowptr: int64[n+1], rowptr[0] = 0, non-decreasing; col: int32[nnz], within a row strictly
+ * increasing and >= the row index (upper triangle); val: nnz values of val_type
+ * (EIG_BF16 = uint16 bfloat16 bit patterns).  on_device selects host or device pointers. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const void* val;
+  eig_dtype val_type;
+  int on_device;
+} eig_csr_upper;
+
+/* ------------------------------------------------------------------------------------ *
+ * Library                                                                              *
+ * ------------------------------------------------------------------------------------ */
+
+/* Human-readable name of a status code (static string). */
+EIG_API const char* eig_strerror(eig_status s);
+/* Message of the last CUDA error seen by this library on the calling thread ("" if none). */
+EIG_API const char* eig_last_cuda_error(void);
+/* Version string of the build, e.g. "0.1.0 sm_103a". */
+EIG_API const char* eig_version(void);
+/* Number of CUDA kernel launches this library has made in this process (all threads). */
+EIG_API int64_t eig_launch_count(void);
+
+/* ------------------------------------------------------------------------------------ *
+ * Step-level entry points (device pointers) -- one per hot-path step                    *
+ * ------------------------------------------------------------------------------------ */
+
+/* Symmetric half-stored SpMM plan.
+ * The product Y = H X of Sec. 1 / Eqs. (upd1)-(upd2) with H given by its upper triangle U:
+ * Y = U X + U_strict^T X, each stored off-diagonal h_ij applied as both H_ij and H_ji.
+ * The plan copies H to device memory it owns (when H->on_device = 0, or always when
+ * copy = 1) and builds the tile lists and the transpose schedule of the atomic-free
+ * scatter: rows are grouped in row blocks of `row_block` rows (multiple of 32, <= 512),
+ * columns in column blocks of `col_block` columns (multiple of 32, <= row_block, dividing
+ * row_block).  0 selects defaults (256, 128).  When copy = 0 and H is on the device the
+ * plan keeps H's pointers, which must then outlive the plan.
+ * Errors: EIG_EINVAL if the CSR is malformed (checked on device: sortedness, col >= row,
+ * col < n), EIG_ENOMEM, EIG_ECUDA. */
+EIG_API eig_status eig_spmm_plan_create(const eig_csr_upper* H, int row_block, int col_block, int copy,
+                                void* stream, void** plan);
+EIG_API void eig_spmm_plan_destroy(void* plan);
+
+typedef struct {
+  int64_t n, nnz;
+  int row_block, col_block;
+  int64_t n_row_blocks, n_col_blocks;
+  int64_t n_tiles;          /* nonempty (row block, column block) pairs                   */
+  int64_t n_slots;          /* tiles whose transposed part goes through scratch            */
+  int64_t scratch_bytes_per_col;  /* scratch bytes per vector column per byte of element    */
+  eig_dtype val_type;
+} eig_spmm_info;
+EIG_API eig_status eig_spmm_plan_info(const void* plan, eig_spmm_info* info);
+
+/* Y = H X.  X, Y: device, row-major n x nb, element type vec_type (EIG_F32 or EIG_F64),
+ * nb in {1, 2, 4, 8, 16, 32}.  X and Y must not overlap.  Scratch for the transposed
+ * partial products is owned by the plan (grown on demand; the first call for a given
+ * (nb, vec_type) may allocate).  Deterministic: results are bitwise reproducible.
+ * Supported (matrix, vector) types: (F32,F32), (F64,F64), (BF16,F32), (F32,F64). */
+EIG_API eig_status eig_spmm(void* plan, const void* X, void* Y, int nb, eig_dtype vec_type, void* stream);
+
+/* Gram product G = A^T B (Eq. rreig's S^T S / S^T H S; Eq. bgs's V^T W).  A, B: device, row-major
+ * n x nb of vec_type (F32 or F64), nb <= 64; G: device FP64 nb x nb (row-major).  FP32 inputs:
+ * products in FP32, 32-row partial sums accumulated in double-float (two FP32 words), CTA
+ * partials in FP64, fixed-order reduction (bitwise reproducible).  Per-call scratch is taken
+ * stream-ordered (cudaMallocAsync) and released on the same stream. */
+EIG_API eig_status eig_gram(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type, double* G,
+                            void* stream);
+
+/* CholeskyQR2 (Alg. 3 "CholeskyQR"; applied twice): X (device, n x k, vec_type, in place) becomes
+ * Q with X_in = Q R, R (device FP64 k x k, upper triangular) = R2 R1.  k <= 64.  Returns
+ * EIG_EBREAKDOWN when a squared Cholesky pivot falls below 1e-14 * max diag of the Gram
+ * (X numerically rank deficient); X is then left partially updated. */
+EIG_API eig_status eig_cholqr2(void* X, int64_t n, int k, eig_dtype vec_type, double* R, void* stream);
+
+/* Lowest m eigenpairs of the symmetric k x k matrix A (device FP64, row-major; only its
+ * symmetric part is used): w[m] ascending, Z (k x m row-major, orthonormal columns).  The
+ * projected problems of Alg. 1 ("T U = U Theta"), Alg. 3 ("T S = S Theta").  k <= 1024,
+ * m <= min(k, 256).  Householder tridiagonalisation, bisection, inverse iteration (FP64). */
+EIG_API eig_status eig_small_syev(const double* A, int k, int m, double* w, double* Z, void* stream);
+
+/* Rayleigh-Ritz on the pencil (A, G) = (S^T H S, S^T S) of Eq. (rreig): the nb leftmost
+ * eigenpairs, theta[nb] and C (k x nb, row-major) with C^T G C = I (all device FP64).  G is
+ * scaled to unit diagonal and Cholesky-factored; *info_host (host int) = 0 on success, 1 when a
+ * squared pivot fell below piv_tol (numerically dependent basis; C is then undefined). */
+EIG_API eig_status eig_small_rr(const double* A, const double* G, int k, int nb, double piv_tol, double* theta,
+                                double* C, int* info_host, void* stream);
+
+/* 2x2 Rayleigh-Ritz of RMM-DIIS (Eqs. rr, xuwg) for m columns: dots (device FP64 m x 6 rows
+ * <x,x>, <x,Hx>, <x,r>, <r,r>, <x,Hr>, <r,Hr>) -> theta[m] (smaller eigenvalue of the pencil)
+ * and g[m][2] with g^T (W^T W) g = 1, g1 <= 0 (the orientation of LAPACK's generalized solver;
+ * consecutive RMM-DIIS iterates alternate in sign).  active (device int[m]): 0 leaves the column on
+ * x (g = (1/||x||, 0)). */
+EIG_API eig_status eig_rmm_rr2(const double* dots, const int* active, int m, double* theta, double* g,
+                               void* stream);
+
+/* DIIS coefficients of Eqs. (xsum)-(rmm) for m columns: B (device FP64 [m][20][20]) holds the
+ * residual Gram <r^(i), r^(k)> by history slot; slots (host int[s], oldest first, s <= 20)
+ * name the window.  alpha (device FP64 [m][20]) receives the coefficients in window order
+ * (sum 1), by the substitution alpha_last = 1 - sum(others) of Sec. 2.5 and a Cholesky solve
+ * that drops the oldest entries while the difference system is numerically singular. */
+EIG_API eig_status eig_rmm_diis(const double* B, const int* slots, int s, const int* active, int m, double* alpha,
+                                void* stream);
+
+/* ------------------------------------------------------------------------------------ *
+ * Solver handle: eig_create / eig_solve / eig_ritz                                     *
+ * ------------------------------------------------------------------------------------ */
+
+typedef struct {
+  double tol;              /* relative residual ||Hz - z theta|| / |theta| (Sec. 3.2); default 1e-6   */
+  int maxiter;             /* iteration limit per phase; default 500                                */
+  eig_method front;        /* hybrid front: EIG_LOBPCG (default) or EIG_BLOCK_LANCZOS (Sec. 4)      */
+  double switch_tau;       /* hybrid: switch when tau (Eq. switchtau) <= switch_tau; default 1e-7;  */
+                           /* <= 0 disables                                                          */
+  double switch_res;       /* hybrid: switch when max rel. residual <= switch_res; default 0 (off)  */
+  int switch_after;        /* hybrid: switch after this many front iterations; 0 = off              */
+  int s_max;               /* DIIS window of Eqs. (xsum)-(rmm), 1..20; default 10 (Sec. 2.6)         */
+  eig_dtype vec_type;      /* vector precision of the SpMM operands and front-phase blocks:         */
+                           /* EIG_F32 (default, FP64 kept for Grams/projected problems/DIIS and the */
+                           /* RMM-DIIS iterates) or EIG_F64 (every vector in FP64)                  */
+  int precond;             /* LOBPCG K^{-1} of Eq. (wblock): 0 none, 1 Jacobi (default)              */
+  int rmm_precond;         /* RMM-DIIS: 0 W = (x~, r~) as Alg. 4 (default), 1 W = (x~, K^{-1} r~)  */
+  double precond_floor;    /* Jacobi: |H_ii - theta| floored at this value; default 0.1             */
+  int cheb_degree;         /* ChebFSI polynomial degree d (Alg. 3); default 10 (Sec. 3.2)           */
+  double lambda_ub;        /* ChebFSI spectrum upper bound; 0 = ten Lanczos steps (Sec. 3.2)        */
+  int lanczos_maxbasis;    /* Lanczos / block Lanczos basis vectors before giving up; default 600   */
+  const double* X0;        /* initial guess, FP64 row-major n x x0_cols, or NULL (seeded random)    */
+  int x0_cols;
+  int x0_on_device;
+  uint64_t seed;           /* seed of the random start when X0 == NULL                              */
+  int certify;             /* recompute true residuals in FP64 at the end (default 1)               */
+  int timing;              /* record per-phase CUDA-event times in eig_stats (default 0)            */
+  void* stream;            /* cudaStream_t; NULL = default stream                                   */
+  double* trace;           /* optional host buffer of trace_cap rows of 2 + 2*n_ev doubles: per     */
+  int trace_cap;           /* iteration [phase (0 front/single, 1 RMM-DIIS), iteration,             */
+                           /* theta_1..theta_nev, relres_1..relres_nev] (the convergence histories  */
+                           /* of Sec. 3.2); NULL = off                                              */
+} eig_opts;
+
+typedef struct {
+  int converged;           /* 1 when all n_ev pairs met tol                                          */
+  int iterations_front;    /* front-method (or single-method) iterations                             */
+  int iterations_rmm;      /* RMM-DIIS iterations (hybrid / rmmdiis)                                 */
+  int switch_reason;       /* hybrid: 0 none, 1 tau, 2 residual, 3 fixed count, 4 front breakdown   */
+  int64_t spmm_calls;      /* products of H with a block                                            */
+  int64_t spmv_count;      /* SpMV count as Sec. 2.6 counts it                                      */
+  double last_tau;         /* last tau of Eq. (switchtau) seen by the front                          */
+  double max_relres;       /* max relative residual of the returned pairs (FP64 if certify)         */
+  double time_ms_total;    /* wall time of eig_solve on the stream (timing = 1)                     */
+  double time_ms_spmm;     /* sum of SpMM kernel times (timing = 1)                                 */
+  double time_ms_front;    /* front phase (timing = 1)                                              */
+  double time_ms_rmm;      /* RMM-DIIS phase (timing = 1)                                           */
+  int64_t spmm_timed;      /* SpMM calls included in time_ms_spmm                                   */
+  double spmm_bytes;       /* sum over the solve's SpMM calls of their algorithmic bytes: one read  */
+                           /* of the stored triangle (values + int32 columns) and rowptr, X read   */
+                           /* and Y written once                                                     */
+  int trace_rows;          /* rows written to opts->trace                                           */
+} eig_stats;
+
+/* Fills *o with the defaults documented in eig_opts. */
+EIG_API void eig_default_opts(eig_opts* o);
+
+/* Creates a solver for the n_ev algebraically smallest eigenpairs of H (Sec. 2).  `block` is
+ * the block size n_b >= n_ev of the block methods (Sec. 2.2-2.4; 8 or 16 in the paper); it is
+ * rounded up to a power of two <= 32.  H is copied to device memory owned by the handle and the
+ * SpMM plan is built (see eig_spmm_plan_create).  One handle serves one stream at a time.
+ * Errors: EIG_EINVAL (n_ev < 1, n_ev > block, block > 32, n_ev > n, malformed CSR). */
+EIG_API eig_status eig_create(const eig_csr_upper* H, int n_ev, int block, void** handle);
+EIG_API void eig_destroy(void* handle);
+
+/* Runs a method (opts NULL = defaults).  Returns EIG_OK when every pair met opts->tol,
+ * EIG_ENOT_CONVERGED when maxiter ran out (the best pairs are still kept for eig_ritz),
+ * EIG_EBREAKDOWN when a basis became numerically rank deficient before any usable result,
+ * EIG_EDUPLICATE when RMM-DIIS left two returned vectors on the same eigenvector.
+ * stats may be NULL.  Synchronises opts->stream before returning. */
+EIG_API eig_status eig_solve(void* handle, eig_method method, const eig_opts* opts, eig_stats* stats);
+
+/* Copies the last result: theta[n_ev] (host, ascending), X (FP64 row-major n x n_ev, host when
+ * on_device = 0, device otherwise; may be NULL), relres[n_ev] (host; may be NULL).
+ * EIG_EINVAL when no solve has produced a result yet. */
+EIG_API eig_status eig_ritz(void* handle, double* theta, double* X, double* relres, int on_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIG_H_ */

@@ -18,7 +18,11 @@ Readings:
 * the constrained problem is solved by the substitution alpha_{l-1} = 1 - sum of the
   others (text after Eq. rmm), i.e. an unconstrained least-squares problem in the
   differences r^(i) - r^(l-1), solved with numpy.linalg.lstsq;
-* x^(l) is normalised so that ||x^(l)|| = 1 (g^T (W^T W) g = 1);
+* x^(l) is normalised so that ||x^(l)|| = 1 (g^T (W^T W) g = 1), and the sign of g -- which the
+  paper leaves open, and which the affine DIIS constraint of Eq. (alphasum) is not invariant to --
+  is fixed as g_1 <= 0, the sign LAPACK's generalized symmetric eigensolver returns for these 2x2
+  pencils (so consecutive iterates alternate in sign, as in a MATLAB implementation built on eig);
+  with g_1 >= 0 instead the iteration stagnates on interior pairs of the CI-shaped test matrices;
 * optional preconditioned variant (precond="jacobi"): the 2x2 subspace is
   W = (x~, K^{-1} r~) with the Jacobi K^{-1} of oracle.precond at theta~; the plain
   method of Alg. 4 is precond="none" (the default);
@@ -48,7 +52,7 @@ def diis_coefficients(rs):
 
 def rr2(x, r, Hx, Hr):
     """Smaller eigenpair of the 2x2 pencil (W^T H W, W^T W), W = (x, r) (Eq. rr).
-    Returns (theta, g) with g^T (W^T W) g = 1.  Falls back to the Rayleigh quotient of x
+    Returns (theta, g) with g^T (W^T W) g = 1 and g_1 <= 0.  Falls back to the Rayleigh quotient of x
     when W^T W is numerically singular."""
     A = np.array([[x @ Hx, x @ Hr], [r @ Hx, r @ Hr]], dtype=np.float64)
     A = 0.5 * (A + A.T)
@@ -56,7 +60,8 @@ def rr2(x, r, Hx, Hr):
     B = 0.5 * (B + B.T)
     try:
         w, G = sla.eigh(A, B)
-        return float(w[0]), G[:, 0]
+        g = G[:, 0]
+        return float(w[0]), (-g if g[0] > 0 else g)
     except np.linalg.LinAlgError:
         nx = np.sqrt(B[0, 0])
         return float(A[0, 0] / B[0, 0]), np.array([1.0 / nx, 0.0])

@@ -1,0 +1,354 @@
+"""Thin ctypes binding of libeig.so (argument marshalling only).
+
+Names follow include/eig.h.  Tensors are torch tensors (device memory, streams); host
+arrays may be numpy arrays.  Every arithmetic step happens inside libeig.so; when the
+library is not built, or no CUDA device is present, load() raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libeig.so")
+_lib = None
+
+EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ECUDA, EIG_ENOT_CONVERGED, EIG_EBREAKDOWN, EIG_ETIMEOUT, \
+    EIG_EDUPLICATE, EIG_EUNSUPPORTED = range(9)
+EIG_F64, EIG_F32, EIG_BF16 = 0, 1, 2
+EIG_LANCZOS, EIG_BLOCK_LANCZOS, EIG_LOBPCG, EIG_CHEBFILTER, EIG_RMMDIIS, EIG_HYBRID = range(6)
+METHODS = {"lanczos": 0, "block_lanczos": 1, "lobpcg": 2, "chebfilter": 3, "rmmdiis": 4, "hybrid": 5}
+STORAGE = {"f64": EIG_F64, "f32": EIG_F32, "bf16": EIG_BF16}
+
+
+class EigError(RuntimeError):
+    def __init__(self, status, where):
+        lib = _lib
+        msg = lib.eig_strerror(status).decode() if lib else str(status)
+        extra = lib.eig_last_cuda_error().decode() if (lib and status == EIG_ECUDA) else ""
+        super().__init__(f"{where}: {msg} {extra}".strip())
+        self.status = status
+
+
+class CsrUpper(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("val_type", C.c_int), ("on_device", C.c_int)]
+
+
+class SpmmInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_block", C.c_int), ("col_block", C.c_int),
+                ("n_row_blocks", C.c_int64), ("n_col_blocks", C.c_int64), ("n_tiles", C.c_int64),
+                ("n_slots", C.c_int64), ("scratch_bytes_per_col", C.c_int64), ("val_type", C.c_int)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("front", C.c_int), ("switch_tau", C.c_double),
+                ("switch_res", C.c_double), ("switch_after", C.c_int), ("s_max", C.c_int), ("vec_type", C.c_int),
+                ("precond", C.c_int), ("rmm_precond", C.c_int), ("precond_floor", C.c_double),
+                ("cheb_degree", C.c_int), ("lambda_ub", C.c_double), ("lanczos_maxbasis", C.c_int),
+                ("X0", C.c_void_p), ("x0_cols", C.c_int), ("x0_on_device", C.c_int), ("seed", C.c_uint64),
+                ("certify", C.c_int), ("timing", C.c_int), ("stream", C.c_void_p), ("trace", C.c_void_p),
+                ("trace_cap", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("converged", C.c_int), ("iterations_front", C.c_int), ("iterations_rmm", C.c_int),
+                ("switch_reason", C.c_int), ("spmm_calls", C.c_int64), ("spmv_count", C.c_int64),
+                ("last_tau", C.c_double), ("max_relres", C.c_double), ("time_ms_total", C.c_double),
+                ("time_ms_spmm", C.c_double), ("time_ms_front", C.c_double), ("time_ms_rmm", C.c_double),
+                ("spmm_timed", C.c_int64), ("spmm_bytes", C.c_double), ("trace_rows", C.c_int)]
+
+
+_SIGS = {
+    "eig_strerror": (C.c_char_p, [C.c_int]),
+    "eig_last_cuda_error": (C.c_char_p, []),
+    "eig_version": (C.c_char_p, []),
+    "eig_launch_count": (C.c_int64, []),
+    "eig_spmm_plan_create": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                       C.POINTER(C.c_void_p)]),
+    "eig_spmm_plan_destroy": (None, [C.c_void_p]),
+    "eig_spmm_plan_info": (C.c_int, [C.c_void_p, C.POINTER(SpmmInfo)]),
+    "eig_spmm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "eig_gram": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "eig_cholqr2": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "eig_small_syev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "eig_small_rr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                               C.POINTER(C.c_int), C.c_void_p]),
+    "eig_rmm_rr2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "eig_rmm_diis": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                               C.c_void_p]),
+    "eig_default_opts": (None, [C.POINTER(Opts)]),
+    "eig_create": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "eig_destroy": (None, [C.c_void_p]),
+    "eig_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Opts), C.POINTER(Stats)]),
+    "eig_ritz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+}
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load_symbols_only(path=None):
+    """Load the shared library without touching a GPU (used by the CPU export tests)."""
+    lib = C.CDLL(path or _LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def load():
+    """The library, for use on a CUDA device.  Raises when it is missing or no GPU is present."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is not built; run __graft_entry__.build() (no CPU fallback)")
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libeig needs a CUDA device (no CPU fallback)")
+    torch.cuda.init()
+    _lib = load_symbols_only()
+    return _lib
+
+
+def check(status, where):
+    if status != EIG_OK:
+        raise EigError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    import numpy as np
+    return t.ctypes.data_as(C.c_void_p).value if isinstance(t, np.ndarray) else t
+
+
+def stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def vec_dtype(t):
+    import torch
+    if t.dtype == torch.float32:
+        return EIG_F32
+    if t.dtype == torch.float64:
+        return EIG_F64
+    raise TypeError(f"vector blocks must be float32 or float64, got {t.dtype}")
+
+
+def csr_struct(rowptr, col, val, storage, n, on_device):
+    """eig_csr_upper over numpy (host) or torch (device) arrays; caller keeps the arrays alive."""
+    s = CsrUpper()
+    s.n = int(n)
+    s.nnz = int(col.shape[0])
+    s.rowptr = _ptr(rowptr)
+    s.col = _ptr(col)
+    s.val = _ptr(val)
+    s.val_type = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    s.on_device = 1 if on_device else 0
+    return s
+
+
+class SpmmPlan:
+    """eig_spmm_plan_create / eig_spmm / eig_spmm_plan_destroy."""
+
+    def __init__(self, H, row_block=0, col_block=0, device_arrays=None, copy=True):
+        lib = load()
+        self._keep = None
+        if device_arrays is not None:
+            rp, cl, vl = device_arrays
+            st = csr_struct(rp, cl, vl, H.storage, H.n, True)
+            self._keep = device_arrays
+        else:
+            import numpy as np
+            rp, cl, vl = (np.ascontiguousarray(H.rowptr), np.ascontiguousarray(H.col),
+                          np.ascontiguousarray(H.val))
+            st = csr_struct(rp, cl, vl, H.storage, H.n, False)
+        self.n = H.n
+        h = C.c_void_p()
+        check(lib.eig_spmm_plan_create(C.byref(st), int(row_block), int(col_block), 1 if copy else 0,
+                                       stream_ptr(), C.byref(h)), "eig_spmm_plan_create")
+        self._h = h
+        self._lib = lib
+
+    def info(self):
+        inf = SpmmInfo()
+        check(self._lib.eig_spmm_plan_info(self._h, C.byref(inf)), "eig_spmm_plan_info")
+        return {k: getattr(inf, k) for k, _ in SpmmInfo._fields_}
+
+    def spmm(self, X, Y=None, stream=None):
+        import torch
+        assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == self.n
+        if Y is None:
+            Y = torch.empty_like(X)
+        check(self._lib.eig_spmm(self._h, _ptr(X), _ptr(Y), int(X.shape[1]), vec_dtype(X), stream_ptr(stream)),
+              "eig_spmm")
+        return Y
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.eig_spmm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------------------
+# step-level calls (device tensors)
+# ---------------------------------------------------------------------------------------
+def gram(A, B):
+    """G = A^T B (FP64 nb x nb) through eig_gram."""
+    import torch
+    lib = load()
+    assert A.shape == B.shape and A.dtype == B.dtype and A.is_contiguous() and B.is_contiguous()
+    G = torch.empty(A.shape[1], A.shape[1], dtype=torch.float64, device=A.device)
+    check(lib.eig_gram(_ptr(A), _ptr(B), A.shape[0], A.shape[1], vec_dtype(A), _ptr(G), stream_ptr()), "eig_gram")
+    return G
+
+
+def cholqr2(X):
+    """In-place CholeskyQR2: returns (Q (= X), R)."""
+    import torch
+    lib = load()
+    assert X.is_contiguous()
+    R = torch.empty(X.shape[1], X.shape[1], dtype=torch.float64, device=X.device)
+    check(lib.eig_cholqr2(_ptr(X), X.shape[0], X.shape[1], vec_dtype(X), _ptr(R), stream_ptr()), "eig_cholqr2")
+    return X, R
+
+
+def small_syev(A, m):
+    import torch
+    lib = load()
+    k = A.shape[0]
+    w = torch.empty(m, dtype=torch.float64, device=A.device)
+    Z = torch.empty(k, m, dtype=torch.float64, device=A.device)
+    check(lib.eig_small_syev(_ptr(A.contiguous()), k, m, _ptr(w), _ptr(Z), stream_ptr()), "eig_small_syev")
+    return w, Z
+
+
+def small_rr(A, G, nb, piv_tol=1e-13):
+    import torch
+    lib = load()
+    k = A.shape[0]
+    th = torch.empty(nb, dtype=torch.float64, device=A.device)
+    Cm = torch.empty(k, nb, dtype=torch.float64, device=A.device)
+    info = C.c_int(0)
+    check(lib.eig_small_rr(_ptr(A.contiguous()), _ptr(G.contiguous()), k, nb, float(piv_tol), _ptr(th), _ptr(Cm),
+                           C.byref(info), stream_ptr()), "eig_small_rr")
+    return th, Cm, info.value
+
+
+def rmm_rr2(dots, active):
+    import torch
+    lib = load()
+    m = dots.shape[0]
+    th = torch.empty(m, dtype=torch.float64, device=dots.device)
+    g = torch.empty(m, 2, dtype=torch.float64, device=dots.device)
+    check(lib.eig_rmm_rr2(_ptr(dots.contiguous()), _ptr(active), m, _ptr(th), _ptr(g), stream_ptr()), "eig_rmm_rr2")
+    return th, g
+
+
+def rmm_diis(B, slots, active):
+    import torch
+    lib = load()
+    m = B.shape[0]
+    alpha = torch.empty(m, 20, dtype=torch.float64, device=B.device)
+    arr = (C.c_int * len(slots))(*slots)
+    check(lib.eig_rmm_diis(_ptr(B.contiguous()), arr, len(slots), _ptr(active), m, _ptr(alpha), stream_ptr()),
+          "eig_rmm_diis")
+    return alpha
+
+
+# ---------------------------------------------------------------------------------------
+# solver handle
+# ---------------------------------------------------------------------------------------
+class Solver:
+    """eig_create / eig_solve / eig_ritz / eig_destroy."""
+
+    def __init__(self, H, n_ev, block):
+        import numpy as np
+        self._lib = lib = load()
+        rp, cl, vl = (np.ascontiguousarray(H.rowptr), np.ascontiguousarray(H.col), np.ascontiguousarray(H.val))
+        st = csr_struct(rp, cl, vl, H.storage, H.n, False)
+        h = C.c_void_p()
+        check(lib.eig_create(C.byref(st), int(n_ev), int(block), C.byref(h)), "eig_create")
+        self._h = h
+        self.n, self.n_ev = H.n, n_ev
+
+    def solve(self, method="hybrid", X0=None, **opts):
+        """Runs a method; returns (status, stats dict).  X0: numpy (host) or torch (device) FP64
+        n x k array.  Keyword options map to eig_opts fields (vec_type as 'f32'/'f64',
+        front as a method name)."""
+        import numpy as np
+        o = Opts()
+        self._lib.eig_default_opts(C.byref(o))
+        keep = None
+        for k, v in opts.items():
+            if k == "vec_type":
+                v = STORAGE[v] if isinstance(v, str) else v
+            if k == "front":
+                v = METHODS[v] if isinstance(v, str) else v
+            setattr(o, k, v)
+        if X0 is not None:
+            if hasattr(X0, "data_ptr"):
+                assert X0.dtype.is_floating_point and X0.element_size() == 8 and X0.is_contiguous()
+                o.X0 = X0.data_ptr()
+                o.x0_on_device = 1
+                keep = X0
+            else:
+                keep = np.ascontiguousarray(X0, dtype=np.float64)
+                o.X0 = keep.ctypes.data_as(C.c_void_p).value
+                o.x0_on_device = 0
+            o.x0_cols = int(keep.shape[1])
+        if not o.stream:
+            o.stream = stream_ptr()
+        tr = None
+        if opts.get("trace_cap", 0):
+            tr = np.zeros((int(opts["trace_cap"]), 2 + 2 * self.n_ev))
+            o.trace = tr.ctypes.data_as(C.c_void_p).value
+        stats = Stats()
+        rc = self._lib.eig_solve(self._h, METHODS[method] if isinstance(method, str) else int(method), C.byref(o),
+                                 C.byref(stats))
+        del keep
+        if rc not in (EIG_OK, EIG_ENOT_CONVERGED, EIG_EDUPLICATE):
+            raise EigError(rc, "eig_solve")
+        st = {k: getattr(stats, k) for k, _ in Stats._fields_}
+        if tr is not None:
+            st["trace"] = tr[: stats.trace_rows].copy()
+        return rc, st
+
+    def ritz(self, X_on_device=False):
+        """(theta[n_ev], X (n x n_ev FP64; numpy or torch), relres[n_ev])."""
+        import numpy as np
+        th = np.zeros(self.n_ev)
+        rel = np.zeros(self.n_ev)
+        if X_on_device:
+            import torch
+            X = torch.empty(self.n, self.n_ev, dtype=torch.float64, device="cuda")
+            check(self._lib.eig_ritz(self._h, _ptr(th), _ptr(X), _ptr(rel), 1), "eig_ritz")
+        else:
+            X = np.zeros((self.n, self.n_ev))
+            check(self._lib.eig_ritz(self._h, _ptr(th), _ptr(X), _ptr(rel), 0), "eig_ritz")
+        return th, X, rel
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.eig_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

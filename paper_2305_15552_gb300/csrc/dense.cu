@@ -1,0 +1,418 @@
+// Tall-skinny dense kernels: Gram products (Eq. rreig's S^T S and S^T H S; Eq. bgs's V^T W),
+// block-times-small-matrix products (Eqs. xupd, pupd; CholQR's X R^{-1}), the fused LOBPCG
+// update, and deterministic reductions.  All are HBM-bound passes over n x nb blocks.
+#include "common.cuh"
+#include "dense.cuh"
+#include "vec.cuh"
+
+namespace eig {
+
+// ---------------------------------------------------------------------------------------
+// double-float accumulation in FP32 (Knuth TwoSum + Fast2Sum)
+// ---------------------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add(DF& a, float x) {
+  const float s = a.hi + x;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (x - bb);
+  const float e = err + a.lo;
+  const float h = s + e;
+  a.lo = e - (h - s);
+  a.hi = h;
+}
+
+template <typename T> struct Acc;  // chunk accumulator type per vector type
+template <> struct Acc<float> { typedef DF type; };
+template <> struct Acc<double> { typedef double type; };
+
+__device__ __forceinline__ void acc_zero(DF& a) { a.hi = 0.f; a.lo = 0.f; }
+__device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void acc_add(DF& a, float x) { df_add(a, x); }
+__device__ __forceinline__ void acc_add(double& a, double x) { a += x; }
+__device__ __forceinline__ double acc_get(const DF& a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double acc_get(const double& a) { return a; }
+
+constexpr int kGramThreads = 256;
+constexpr int kGramRows = 32;
+
+struct PairList {
+  int a[kMaxPairs], b[kMaxPairs];
+  int n;
+};
+
+// Thread t owns tiles t, t+256, ... of the (pair, ti, tj) grid of TM x TM tiles.
+template <typename T, int TM, int MAXT>
+__global__ void __launch_bounds__(kGramThreads)
+k_gram(BlockList blocks, PairList pairs, int nb, int64_t n, int64_t rows_per_cta, double* part) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);  // [nblocks][kGramRows][nb]
+  typedef typename Acc<T>::type A;
+  const int tpp = (nb / TM) * (nb / TM);
+  const int ntiles = pairs.n * tpp;     // <= MAXT * kGramThreads
+  A acc[MAXT][TM][TM];
+  T cacc[MAXT][TM][TM];
+#pragma unroll
+  for (int s = 0; s < MAXT; ++s)
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TM; ++j) { acc_zero(acc[s][i][j]); cacc[s][i][j] = T(0); }
+  const int64_t r0 = blockIdx.x * rows_per_cta;
+  const int64_t r1 = min64(n, r0 + rows_per_cta);
+  for (int64_t rc = r0; rc < r1; rc += kGramRows) {
+    const int rows = (int)min64(kGramRows, r1 - rc);
+    __syncthreads();
+    for (int b = 0; b < blocks.n; ++b) {
+      const T* src = static_cast<const T*>(blocks.p[b]) + rc * nb;
+      T* dst = sm + (size_t)b * kGramRows * nb;
+      for (int i = threadIdx.x; i < kGramRows * nb; i += blockDim.x) dst[i] = (i < rows * nb) ? src[i] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < MAXT; ++s) {
+      const int tile = threadIdx.x + s * kGramThreads;
+      if (tile < ntiles) {
+        const int q = tile / tpp, rem = tile % tpp;
+        const int ti = (rem / (nb / TM)) * TM, tj = (rem % (nb / TM)) * TM;
+        const T* Ab = sm + (size_t)pairs.a[q] * kGramRows * nb;
+        const T* Bb = sm + (size_t)pairs.b[q] * kGramRows * nb;
+        for (int r = 0; r < kGramRows; ++r) {
+          T av[TM], bv[TM];
+#pragma unroll
+          for (int i = 0; i < TM; ++i) { av[i] = Ab[r * nb + ti + i]; bv[i] = Bb[r * nb + tj + i]; }
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TM; ++j) cacc[s][i][j] = fma(av[i], bv[j], cacc[s][i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TM; ++j) { acc_add(acc[s][i][j], cacc[s][i][j]); cacc[s][i][j] = T(0); }
+      }
+    }
+  }
+  double* out = part + (size_t)blockIdx.x * pairs.n * nb * nb;
+#pragma unroll
+  for (int s = 0; s < MAXT; ++s) {
+    const int tile = threadIdx.x + s * kGramThreads;
+    if (tile < ntiles) {
+      const int q = tile / tpp, rem = tile % tpp;
+      const int ti = (rem / (nb / TM)) * TM, tj = (rem % (nb / TM)) * TM;
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) out[(size_t)q * nb * nb + (ti + i) * nb + tj + j] = acc_get(acc[s][i][j]);
+    }
+  }
+}
+
+// out[j] = sum over parts in fixed order
+__global__ void k_reduce_partials(const double* __restrict__ part, int nparts, int m, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += part[(size_t)b * m + j];
+  out[j] = s;
+}
+
+static int gram_grid(int64_t n, int64_t* rows_per_cta) {
+  int g = num_sms() * 2;
+  int64_t rpc = (n + g - 1) / g;
+  rpc = ((rpc + kGramRows - 1) / kGramRows) * kGramRows;
+  if (rpc < kGramRows) rpc = kGramRows;
+  g = (int)((n + rpc - 1) / rpc);
+  *rows_per_cta = rpc;
+  return g;
+}
+
+size_t gram_scratch_bytes(int npairs, int nb) { return (size_t)num_sms() * 2 * npairs * nb * nb * 8 + 256; }
+
+eig_status reduce_partials(const double* part, int nparts, int m, double* out, cudaStream_t st) {
+  k_reduce_partials<<<(m + 255) / 256, 256, 0, st>>>(part, nparts, m, out);
+  EIG_LAUNCH_CHECK("k_reduce_partials");
+  return EIG_OK;
+}
+
+template <typename T, int TM>
+static eig_status gram_launch(const BlockList& blocks, const PairList& pl, int nb, int64_t n, double* G, void* part,
+                              cudaStream_t st) {
+  int64_t rpc;
+  const int g = gram_grid(n, &rpc);
+  const size_t sm = (size_t)blocks.n * kGramRows * nb * sizeof(T);
+  const int ntiles = pl.n * (nb / TM) * (nb / TM);
+  auto kern = (ntiles <= kGramThreads) ? k_gram<T, TM, 1>
+              : (ntiles <= 2 * kGramThreads ? k_gram<T, TM, 2> : k_gram<T, TM, 4>);
+  if (sm > 48 * 1024) EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<g, kGramThreads, sm, st>>>(blocks, pl, nb, n, rpc, static_cast<double*>(part));
+  EIG_LAUNCH_CHECK("k_gram");
+  return reduce_partials(static_cast<double*>(part), g, pl.n * nb * nb, G, st);
+}
+
+eig_status gram_multi(const BlockList& blocks, const int* pa, const int* pb, int npairs, int nb, int64_t n,
+                      eig_dtype vt, double* G, void* part, cudaStream_t st) {
+  if (npairs < 1 || npairs > kMaxPairs || nb < 1 || nb > 64 || n < 1 || blocks.n < 1 || blocks.n > 16) return EIG_EINVAL;
+  PairList pl;
+  pl.n = npairs;
+  for (int q = 0; q < npairs; ++q) {
+    if (pa[q] < 0 || pa[q] >= blocks.n || pb[q] < 0 || pb[q] >= blocks.n) return EIG_EINVAL;
+    pl.a[q] = pa[q];
+    pl.b[q] = pb[q];
+  }
+  const int TM = (nb % 4 == 0) ? 4 : ((nb % 2 == 0) ? 2 : 1);
+  if ((size_t)npairs * (nb / TM) * (nb / TM) > 4 * kGramThreads) return EIG_EUNSUPPORTED;
+  if (vt == EIG_F32) {
+    if (TM == 4) return gram_launch<float, 4>(blocks, pl, nb, n, G, part, st);
+    if (TM == 2) return gram_launch<float, 2>(blocks, pl, nb, n, G, part, st);
+    return gram_launch<float, 1>(blocks, pl, nb, n, G, part, st);
+  }
+  if (vt == EIG_F64) {
+    if (TM == 4) return gram_launch<double, 4>(blocks, pl, nb, n, G, part, st);
+    if (TM == 2) return gram_launch<double, 2>(blocks, pl, nb, n, G, part, st);
+    return gram_launch<double, 1>(blocks, pl, nb, n, G, part, st);
+  }
+  return EIG_EINVAL;
+}
+
+// ---------------------------------------------------------------------------------------
+// Out = sum_s In_s M_s (+ beta Out): thread per (row, output column)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_block_apply(BlockList in, int nb, const double* __restrict__ M, int m, T* __restrict__ Out,
+                              double beta, int64_t n) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sM = reinterpret_cast<T*>(sm_raw);  // K x m
+  const int K = in.n * nb;
+  for (int i = threadIdx.x; i < K * m; i += blockDim.x) sM[i] = (T)M[i];
+  __syncthreads();
+  const int64_t total = n * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / m;
+    const int j = (int)(idx % m);
+    T acc = T(0);
+    for (int s = 0; s < in.n; ++s) {
+      const T* row = static_cast<const T*>(in.p[s]) + r * nb;
+      const T* Ms = sM + (size_t)s * nb * m + j;
+      for (int k = 0; k < nb; ++k) acc = fma(__ldg(row + k), Ms[(size_t)k * m], acc);
+    }
+    if (beta != 0.0) acc = fma((T)beta, Out[idx], acc);
+    Out[idx] = acc;
+  }
+}
+
+eig_status block_apply(const BlockList& in, int nb, const double* M, int m, void* Out, double beta, int64_t n,
+                       eig_dtype vt, cudaStream_t st) {
+  if (in.n < 1 || in.n > kMaxBlocks || nb < 1 || m < 1 || m > 64 || in.n * nb > 1024) return EIG_EINVAL;
+  const int grid = num_sms() * 8;
+  if (vt == EIG_F32) {
+    const size_t sm = (size_t)in.n * nb * m * 4;
+    if (sm > 48 * 1024) EIG_CUDA_TRY(cudaFuncSetAttribute(k_block_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_block_apply<float><<<grid, 256, sm, st>>>(in, nb, M, m, static_cast<float*>(Out), beta, n);
+  } else if (vt == EIG_F64) {
+    const size_t sm = (size_t)in.n * nb * m * 8;
+    if (sm > 48 * 1024) EIG_CUDA_TRY(cudaFuncSetAttribute(k_block_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_block_apply<double><<<grid, 256, sm, st>>>(in, nb, M, m, static_cast<double*>(Out), beta, n);
+  } else {
+    return EIG_EINVAL;
+  }
+  EIG_LAUNCH_CHECK("k_block_apply");
+  return EIG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// conversions, column sums of squares
+// ---------------------------------------------------------------------------------------
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ s, B* __restrict__ d, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (B)s[i];
+}
+
+eig_status convert(const void* src, eig_dtype st_, void* dst, eig_dtype dt_, int64_t count, cudaStream_t st) {
+  const int grid = num_sms() * 8;
+  if (st_ == EIG_F64 && dt_ == EIG_F32) k_convert<double, float><<<grid, 256, 0, st>>>((const double*)src, (float*)dst, count);
+  else if (st_ == EIG_F32 && dt_ == EIG_F64) k_convert<float, double><<<grid, 256, 0, st>>>((const float*)src, (double*)dst, count);
+  else if (st_ == EIG_F64 && dt_ == EIG_F64) k_convert<double, double><<<grid, 256, 0, st>>>((const double*)src, (double*)dst, count);
+  else if (st_ == EIG_F32 && dt_ == EIG_F32) k_convert<float, float><<<grid, 256, 0, st>>>((const float*)src, (float*)dst, count);
+  else return EIG_EINVAL;
+  EIG_LAUNCH_CHECK("k_convert");
+  return EIG_OK;
+}
+
+template <typename T>
+__global__ void k_col_sumsq(const T* __restrict__ X, int k, int64_t n, double* __restrict__ part) {
+  // thread handles column j = tid % k of rows tid/k, tid/k + stride...
+  __shared__ double red[1024];
+  const int rows_per_pass = blockDim.x / k;
+  const int j = threadIdx.x % k, rr = threadIdx.x / k;
+  double s = 0.0;
+  if (rr < rows_per_pass) {
+    for (int64_t r = blockIdx.x * (int64_t)rows_per_pass + rr; r < n; r += (int64_t)gridDim.x * rows_per_pass) {
+      const double v = (double)X[r * k + j];
+      s += v * v;
+    }
+  }
+  red[threadIdx.x] = (rr < rows_per_pass) ? s : 0.0;
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double t = 0.0;
+    for (int q = 0; q < rows_per_pass; ++q) t += red[q * k + threadIdx.x];
+    part[(size_t)blockIdx.x * k + threadIdx.x] = t;
+  }
+}
+
+size_t colsum_scratch_bytes(int k) { return (size_t)num_sms() * 4 * k * 8 + 256; }
+
+eig_status col_sumsq(const void* X, int k, int64_t n, eig_dtype vt, double* out, void* part, cudaStream_t st) {
+  if (k < 1 || k > 256) return EIG_EINVAL;
+  const int grid = num_sms() * 4;
+  const int threads = (256 / k) * k;
+  if (vt == EIG_F32) k_col_sumsq<float><<<grid, threads, 0, st>>>((const float*)X, k, n, (double*)part);
+  else if (vt == EIG_F64) k_col_sumsq<double><<<grid, threads, 0, st>>>((const double*)X, k, n, (double*)part);
+  else return EIG_EINVAL;
+  EIG_LAUNCH_CHECK("k_col_sumsq");
+  return reduce_partials((const double*)part, grid, k, out, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// fused LOBPCG update: thread per (row, column j); a CTA covers rows_per_cta rows
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double jacobi_den(double d, double th, double floor) {
+  double den = d - th;
+  const double mag = fmax(fabs(den), floor);
+  return den < 0.0 ? -mag : mag;
+}
+
+template <typename T>
+__global__ void k_lobpcg_update(T* __restrict__ X, T* __restrict__ W, T* __restrict__ P, T* __restrict__ HX,
+                                const T* __restrict__ HW, T* __restrict__ HP, const double* __restrict__ C, int k,
+                                int nb, const double* __restrict__ theta, const double* __restrict__ diagH,
+                                double floor, int precond, int64_t n, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sC = reinterpret_cast<T*>(sm_raw);       // k x nb
+  double* sTh = reinterpret_cast<double*>(sC + ((k * nb + 1) & ~1));
+  double* red = sTh + nb;                      // blockDim
+  for (int i = threadIdx.x; i < k * nb; i += blockDim.x) sC[i] = (T)C[i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) sTh[i] = theta[i];
+  __syncthreads();
+  const int rpp = blockDim.x / nb;            // rows per pass
+  const int j = threadIdx.x % nb, rr = threadIdx.x / nb;
+  const bool act = rr < rpp;
+  const double th = sTh[j];
+  double rsq = 0.0;
+  // the loop bound is uniform across the CTA so that __syncwarp sees every lane
+  for (int64_t base = blockIdx.x * (int64_t)rpp; base < n; base += (int64_t)gridDim.x * rpp) {
+    const int64_t r = base + rr;
+    const bool valid = act && r < n;
+    T xn = T(0), hxn = T(0), pn = T(0), hpn = T(0), wn = T(0);
+    if (valid) {
+      const T* xr = X + r * nb;
+      const T* hxr = HX + r * nb;
+      if (k == nb) {
+        xn = xr[j];
+        hxn = hxr[j];
+      } else {
+        T x = T(0), hx = T(0);
+        for (int l = 0; l < nb; ++l) {
+          const T c1 = sC[l * nb + j];
+          x = fma(xr[l], c1, x);
+          hx = fma(hxr[l], c1, hx);
+        }
+        const T* wr = W + r * nb;
+        const T* hwr = HW + r * nb;
+        for (int l = 0; l < nb; ++l) {
+          const T c2 = sC[(nb + l) * nb + j];
+          pn = fma(wr[l], c2, pn);
+          hpn = fma(hwr[l], c2, hpn);
+        }
+        if (k == 3 * nb) {
+          const T* pr = P + r * nb;
+          const T* hpr = HP + r * nb;
+          for (int l = 0; l < nb; ++l) {
+            const T c3 = sC[(2 * nb + l) * nb + j];
+            pn = fma(pr[l], c3, pn);
+            hpn = fma(hpr[l], c3, hpn);
+          }
+        }
+        xn = x + pn;
+        hxn = hx + hpn;
+      }
+      const T res = hxn - (T)th * xn;
+      rsq += (double)res * (double)res;
+      wn = res;
+      if (precond == 1) wn = (T)((double)res / jacobi_den(diagH[r], th, floor));
+    }
+    __syncwarp();  // the nb lanes of a row (one warp) have read their inputs before any write
+    if (valid) {
+      if (k != nb) {
+        X[r * nb + j] = xn;
+        HX[r * nb + j] = hxn;
+        P[r * nb + j] = pn;
+        HP[r * nb + j] = hpn;
+      }
+      W[r * nb + j] = wn;
+    }
+  }
+  red[threadIdx.x] = act ? rsq : 0.0;
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    double t = 0.0;
+    for (int q = 0; q < rpp; ++q) t += red[q * nb + threadIdx.x];
+    part[(size_t)blockIdx.x * nb + threadIdx.x] = t;
+  }
+}
+
+int update_grid(int64_t n) {
+  int64_t g = (n + 15) / 16;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+eig_status lobpcg_update(void* X, void* W, void* P, void* HX, void* HW, void* HP, const double* C, int k, int nb,
+                         const double* theta, const double* diagH, double floor, int precond, int64_t n,
+                         eig_dtype vt, double* part, int nparts_max, int* nparts_out, cudaStream_t st) {
+  if (nb < 1 || nb > 32 || 32 % nb != 0 || (k != nb && k != 2 * nb && k != 3 * nb)) return EIG_EINVAL;
+  const int grid = update_grid(n);
+  if (grid > nparts_max) return EIG_EINVAL;
+  const int threads = 256;
+  const size_t sm = (size_t)((k * nb + 1) & ~1) * (vt == EIG_F64 ? 8 : 4) + (size_t)nb * 8 + threads * 8;
+  if (vt == EIG_F32) {
+    k_lobpcg_update<float><<<grid, threads, sm, st>>>((float*)X, (float*)W, (float*)P, (float*)HX, (const float*)HW,
+                                                      (float*)HP, C, k, nb, theta, diagH, floor, precond, n, part);
+  } else if (vt == EIG_F64) {
+    k_lobpcg_update<double><<<grid, threads, sm, st>>>((double*)X, (double*)W, (double*)P, (double*)HX,
+                                                       (const double*)HW, (double*)HP, C, k, nb, theta, diagH, floor,
+                                                       precond, n, part);
+  } else {
+    return EIG_EINVAL;
+  }
+  EIG_LAUNCH_CHECK("k_lobpcg_update");
+  *nparts_out = grid;
+  return EIG_OK;
+}
+
+template <typename T>
+__global__ void k_jacobi(T* __restrict__ R, const double* __restrict__ theta, const double* __restrict__ diagH,
+                         double floor, int nb, int64_t n) {
+  const int64_t total = n * nb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / nb;
+    const int j = (int)(i % nb);
+    R[i] = (T)((double)R[i] / jacobi_den(diagH[r], theta[j], floor));
+  }
+}
+
+eig_status jacobi_block(void* R, const double* theta, const double* diagH, double floor, int nb, int64_t n,
+                        eig_dtype vt, cudaStream_t st) {
+  const int grid = num_sms() * 8;
+  if (vt == EIG_F32) k_jacobi<float><<<grid, 256, 0, st>>>((float*)R, theta, diagH, floor, nb, n);
+  else if (vt == EIG_F64) k_jacobi<double><<<grid, 256, 0, st>>>((double*)R, theta, diagH, floor, nb, n);
+  else return EIG_EINVAL;
+  EIG_LAUNCH_CHECK("k_jacobi");
+  return EIG_OK;
+}
+
+}  // namespace eig

@@ -1,0 +1,58 @@
+// Batched RMM-DIIS kernels (Alg. 4; Sec. 4.3 batches the n_ev refinements into one SpMM).
+#pragma once
+#include "common.cuh"
+
+namespace eig {
+
+constexpr int kRmmSMax = 20;  // largest DIIS window (the paper uses s_max = 10..20)
+
+// Window of history slots, oldest first; slots index the ring buffers.
+struct Window {
+  int slot[kRmmSMax];
+  int s;
+};
+
+// Combine (Eq. xsum) for every column j:  x~ = sum_i a_ji x^(i),
+// Hx~ = sum_i a_ji (r^(i) + theta^(i) x^(i)),  r~ = Hx~ - theta_ref_j x~ (stored in the SpMM
+// vector type; zero for inactive columns), and partial dots <x~,x~>, <x~,Hx~>, <x~,r~>, <r~,r~>,
+// <r~,Hx~> (partials [cta][j][5]).
+// xh: [s_max][n][mp] FP64; rh: [s_max][n][mp] (vt); thh: [s_max][mp]; alpha: [mp][kRmmSMax].
+eig_status rmm_combine(const double* xh, const void* rh, const double* thh, const double* alpha, Window win,
+                       const double* theta_ref, const int* active, int mp, int64_t n, eig_dtype vt, double* xt,
+                       double* hxt, void* rt, double* part, int* nparts, cudaStream_t st);
+
+// Partial dots <x~, H r~>, <r~, H r~>.
+eig_status rmm_dots2(const double* xt, const void* rt, const void* hrt, int mp, int64_t n, eig_dtype vt, double* part,
+                     int* nparts, cudaStream_t st);
+
+// 2x2 Rayleigh-Ritz (Eqs. rr, xuwg) per column from the six dots (dots: [mp][6] = <x,x>, <x,Hx>,
+// <x,r>, <r,r>, <x,Hr>, <r,Hr>): theta (lower root of the pencil) and g = (g1, g2) with
+// g^T (W^T W) g = 1 and g1 <= 0.  Inactive columns get g = (1/||x~||, 0), theta = <x,Hx>/<x,x>.
+eig_status rmm_rr2(const double* dots, const int* active, int mp, double* theta, double* g, cudaStream_t st);
+
+// Update (Eq. xuwg): x = g1 x~ + g2 r~, Hx = g1 Hx~ + g2 H r~, r = Hx - theta x, written to the
+// history slot `slot_new` (x FP64, r in vt); partials of ||r||^2 (FP64 r) and of
+// <r, r^(i)> for the slots of `win_after` (the window including the new slot).
+eig_status rmm_update(const double* xt, const double* hxt, const void* rt, const void* hrt, const double* g,
+                      const double* theta, int slot_new, Window win_after, int mp, int64_t n, eig_dtype vt,
+                      double* xh, void* rh, double* thh, double* part, int* nparts, cudaStream_t st);
+
+// Start of Alg. 4 (lines 2-4) from a given (x, Hx): theta = num/xnorm2 with num = <x,Hx>,
+// x/||x|| written to xh[slot], r = (Hx - theta x)/||x|| to rh[slot] (vt), theta to thh[slot]
+// and theta_out; partials [cta][j][2] of ||r||^2 (FP64 r) and <rq, rq> (rounded r).
+eig_status rmm_start(double* x, const double* hx, const double* num, const double* xnorm2, int mp, int64_t n,
+                     eig_dtype vt, int slot, double* xh, void* rh, double* thh, double* theta_out, double* part,
+                     int* nparts, cudaStream_t st);
+
+// DIIS least squares (Eqs. alphasum, rmm) by the substitution alpha_last = 1 - sum(others):
+// Cholesky of the (s-1)x(s-1) normal matrix of the residual differences, dropping the oldest
+// entries while it is numerically singular.  B: [mp][kRmmSMax][kRmmSMax] Gram of the residual
+// history by slot.  Inactive columns get alpha = one-hot on the newest slot.
+eig_status rmm_diis(const double* B, Window win, const int* active, int mp, double* alpha, cudaStream_t st);
+
+// B[j][slot_new][slot_i] = B[j][slot_i][slot_new] = sums[j][1 + i] for i < win.s (sums: [mp][1+kRmmSMax]).
+eig_status rmm_store_gram(double* B, const double* sums, Window win_after, int slot_new, int mp, cudaStream_t st);
+
+int rmm_grid(int64_t n, int mp);
+
+}  // namespace eig

@@ -1,0 +1,164 @@
+"""GPU eigensolvers through eig_create / eig_solve / eig_ritz against the FP64 oracle: the
+eigenvalues must agree to |dlambda|/|lambda| <= 1e-6 and the returned pairs must have true
+relative residuals <= tol (recomputed here by the oracle's FP64 SpMM)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import ci_matrix, laplacian_kron, laplacian_kron_eigs, principal_submatrix, pad_rows, random_block
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def Solver(H, nev, nb):
+    from paper_2305_15552_gb300.binding import Solver as S
+    return S(H, nev, nb)
+
+
+def guess(H, nb, n0=None):
+    """Zero-padded eigenvectors of the leading principal block (the smaller-model-space guess)."""
+    n0 = n0 or max(nb * 4, H.n // 10)
+    _, Z = O.lowest_eigpairs(O.to_dense(principal_submatrix(H, n0)), nb)
+    return pad_rows(Z, H.n)
+
+
+def check_result(H, S, lam_ref, tol=1e-6, rel_lam=1e-6):
+    th, X, rel = S.ritz()
+    np.testing.assert_allclose(th, lam_ref, rtol=rel_lam, atol=0)
+    tr = O.true_relres(H, th, X)
+    assert np.all(tr <= tol * 1.05), tr
+    np.testing.assert_allclose(rel, tr, rtol=1e-3, atol=1e-12)
+    return th, X
+
+
+@pytest.fixture(scope="module")
+def H3000():
+    H = ci_matrix(3000, 100, 64, seed=1, storage="f64")
+    lam, _ = O.lowest_eigpairs(O.to_dense(H), 12)
+    return H, lam
+
+
+@pytest.fixture(scope="module")
+def H3000f():
+    H = ci_matrix(3000, 100, 64, seed=1, storage="f32")
+    lam, _ = O.lowest_eigpairs(O.to_dense(H), 12)
+    return H, lam
+
+
+def test_lobpcg_fp64(H3000):
+    H, lam = H3000
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("lobpcg", X0=guess(H, 8), vec_type="f64")
+    assert rc == 0 and st["converged"] == 1
+    check_result(H, S, lam[:5])
+
+
+def test_lobpcg_fp64_random_start_laplacian():
+    dims = [9, 11, 13]
+    H = laplacian_kron(dims)
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("lobpcg", vec_type="f64", maxiter=800, seed=3)
+    assert rc == 0
+    check_result(H, S, laplacian_kron_eigs(dims)[:5])
+
+
+@pytest.mark.parametrize("vt", ["f32", "f64"])
+def test_hybrid_lobpcg_rmmdiis(H3000f, vt):
+    H, lam = H3000f
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type=vt, trace_cap=1000)
+    tr = st.pop("trace")
+    msg = f"{st}\n" + "\n".join(" ".join(f"{v:.3e}" for v in row) for row in tr)
+    assert rc == 0, msg
+    assert st["iterations_rmm"] > 0 and st["switch_reason"] == 1, msg
+    th, _, _ = S.ritz()
+    assert np.allclose(th, lam[:5], rtol=1e-6), msg
+    check_result(H, S, lam[:5])
+
+
+def test_hybrid_nev8_nb16(H3000f):
+    H, lam = H3000f
+    S = Solver(H, 8, 16)
+    rc, st = S.solve("hybrid", X0=guess(H, 16), vec_type="f32")
+    assert rc == 0, st
+    check_result(H, S, lam[:8])
+
+
+def test_rmmdiis_from_close_guess(H3000):
+    H, lam = H3000
+    _, Z = O.lowest_eigpairs(O.to_dense(H), 5)
+    X0 = Z + 1e-5 * random_block(H.n, 5, 11)
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("rmmdiis", X0=X0, vec_type="f64", s_max=20, maxiter=400)
+    assert rc == 0, st
+    check_result(H, S, lam[:5])
+
+
+def test_lobpcg_c1_size_fp64():
+    """n = 20,000, ~100 nnz/row, 64-tiles, FP64 (the plain FP64 LOBPCG configuration)."""
+    H = ci_matrix(20000, 100, 64, seed=1, storage="f64")
+    X0 = guess(H, 8, 2000)
+    ref = O.lobpcg(H, X0, 5, tol=1e-10, maxiter=300)
+    assert ref.converged
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("lobpcg", X0=X0, vec_type="f64")
+    assert rc == 0, st
+    check_result(H, S, ref.theta[:5])
+
+
+def test_invalid_arguments():
+    from paper_2305_15552_gb300 import binding
+    H = ci_matrix(500, 40, 64, seed=1, storage="f64")
+    with pytest.raises(binding.EigError) as e:
+        Solver(H, 9, 8)
+    assert e.value.status == binding.EIG_EINVAL
+    S = Solver(H, 4, 8)
+    with pytest.raises(binding.EigError) as e:
+        S.ritz()
+    assert e.value.status == binding.EIG_EINVAL
+
+
+def test_lanczos_fp64(H3000):
+    H, lam = H3000
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("lanczos", X0=guess(H, 8), vec_type="f64")
+    assert rc == 0, st
+    check_result(H, S, lam[:5])
+
+
+def test_block_lanczos_fp64(H3000):
+    H, lam = H3000
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("block_lanczos", X0=guess(H, 8), vec_type="f64")
+    assert rc == 0, st
+    check_result(H, S, lam[:5])
+
+
+def test_chebfsi_fp64(H3000):
+    H, lam = H3000
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("chebfilter", X0=guess(H, 8), vec_type="f64", cheb_degree=10)
+    assert rc == 0, st
+    check_result(H, S, lam[:5])
+
+
+def test_hybrid_block_lanczos_front(H3000):
+    H, lam = H3000
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type="f64", front="block_lanczos", switch_tau=1e-7)
+    assert rc == 0, st
+    check_result(H, S, lam[:5])
+
+
+def test_lobpcg_trace_monotone(H3000):
+    """Ritz values never increase over LOBPCG iterations (nested subspaces) and stay above the
+    exact eigenvalues (Cauchy interlacing)."""
+    H, lam = H3000
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("lobpcg", X0=guess(H, 8), vec_type="f64", trace_cap=500)
+    tr = st["trace"]
+    assert tr.shape[0] == st["iterations_front"] + 1
+    th = tr[:, 2:7]
+    assert np.all(np.diff(th, axis=0) <= 1e-10 * np.abs(th[1:]))
+    assert np.all(th >= lam[:5] - 1e-10)

@@ -65,6 +65,7 @@ def test_rr2_closed_form():
     assert abs(th - root) < 1e-10 * abs(root)
     w = g[0] * x + g[1] * r
     assert abs(w @ w - 1) < 1e-12
+    assert g[0] <= 0
 
 
 def test_diis_two_vector_closed_form():
