@@ -131,6 +131,7 @@ EIG_API eig_status eig_spmm(void* plan, const void* X, void* Y, int nb, eig_dtyp
 EIG_API eig_status eig_gram(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type, double* G,
                             void* stream);
 
+
 /* CholeskyQR2 (Alg. 3 "CholeskyQR"; applied twice): X (device, n x k, vec_type, in place) becomes
  * Q with X_in = Q R, R (device FP64 k x k, upper triangular) = R2 R1.  k <= 64.  Returns
  * EIG_EBREAKDOWN when a squared Cholesky pivot falls below 1e-14 * max diag of the Gram
@@ -205,7 +206,8 @@ typedef struct {
   int converged;           /* 1 when all n_ev pairs met tol                                          */
   int iterations_front;    /* front-method (or single-method) iterations                             */
   int iterations_rmm;      /* RMM-DIIS iterations (hybrid / rmmdiis)                                 */
-  int switch_reason;       /* hybrid: 0 none, 1 tau, 2 residual, 3 fixed count, 4 front breakdown   */
+  int switch_reason;       /* hybrid: 0 none, 1 tau, 2 residual, 3 fixed count, 4 front breakdown, */
+                           /* 5 front residuals rising (instability)                               */
   int64_t spmm_calls;      /* products of H with a block                                            */
   int64_t spmv_count;      /* SpMV count as Sec. 2.6 counts it                                      */
   double last_tau;         /* last tau of Eq. (switchtau) seen by the front                          */

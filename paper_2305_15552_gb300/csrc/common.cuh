@@ -115,6 +115,18 @@ template <> struct ValLoad<uint16_t> {
   }
 };
 
+// Value from a shared-memory (or any generic) pointer, widened to the arithmetic type.
+template <typename V> struct ValSmem;
+template <> struct ValSmem<float> {
+  __device__ __forceinline__ static float get(const float* p, int i) { return p[i]; }
+};
+template <> struct ValSmem<double> {
+  __device__ __forceinline__ static double get(const double* p, int i) { return p[i]; }
+};
+template <> struct ValSmem<uint16_t> {
+  __device__ __forceinline__ static float get(const uint16_t* p, int i) { return bf16_to_f32(p[i]); }
+};
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -94,6 +94,38 @@ k_rmm_dots2(const double* __restrict__ xt, const T* __restrict__ rt, const T* __
   cta_colreduce<2>(v, mp, red, part);
 }
 
+// Preconditioned correction of RMM-DIIS: r~ = K^{-1}(H x~ - theta~ x~), theta~ = <x~,Hx~>/<x~,x~>
+// taken from the combine sums (stride 5); Jacobi K with |H_ii - theta~| floored.
+template <typename T>
+__global__ void k_rmm_precond_resid(const double* __restrict__ xt, const double* __restrict__ hxt,
+                                    const double* __restrict__ sums, const int* __restrict__ active,
+                                    const double* __restrict__ diagH, double floor, int mp, int64_t n,
+                                    T* __restrict__ rt) {
+  const int64_t total = n * mp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % mp);
+    if (!active[j]) { rt[i] = T(0); continue; }
+    const double xx = sums[j * 5 + 0];
+    const double th = xx > 0.0 ? sums[j * 5 + 1] / xx : 0.0;
+    double den = diagH[i / mp] - th;
+    const double mag = fmax(fabs(den), floor);
+    den = den < 0.0 ? -mag : mag;
+    rt[i] = (T)((hxt[i] - th * xt[i]) / den);
+  }
+}
+
+eig_status rmm_precond_resid(const double* xt, const double* hxt, const double* sums, const int* active,
+                             const double* diagH, double floor, int mp, int64_t n, eig_dtype vt, void* rt,
+                             cudaStream_t st) {
+  const int grid = num_sms() * 8;
+  if (vt == EIG_F32)
+    k_rmm_precond_resid<float><<<grid, 256, 0, st>>>(xt, hxt, sums, active, diagH, floor, mp, n, (float*)rt);
+  else
+    k_rmm_precond_resid<double><<<grid, 256, 0, st>>>(xt, hxt, sums, active, diagH, floor, mp, n, (double*)rt);
+  EIG_LAUNCH_CHECK("k_rmm_precond_resid");
+  return EIG_OK;
+}
+
 __global__ void k_rmm_rr2(const double* __restrict__ dots, const int* __restrict__ active, int mp,
                           double* __restrict__ theta, double* __restrict__ g) {
   const int j = threadIdx.x;

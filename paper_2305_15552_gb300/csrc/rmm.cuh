@@ -21,6 +21,12 @@ eig_status rmm_combine(const double* xh, const void* rh, const double* thh, cons
                        const double* theta_ref, const int* active, int mp, int64_t n, eig_dtype vt, double* xt,
                        double* hxt, void* rt, double* part, int* nparts, cudaStream_t st);
 
+// Preconditioned correction r~ = K^{-1}(H x~ - theta~ x~) with theta~ the Rayleigh quotient of x~
+// (from the combine sums, stride 5) and the Jacobi K of the LOBPCG step; zero for inactive columns.
+eig_status rmm_precond_resid(const double* xt, const double* hxt, const double* sums, const int* active,
+                             const double* diagH, double floor, int mp, int64_t n, eig_dtype vt, void* rt,
+                             cudaStream_t st);
+
 // Partial dots <x~, H r~>, <r~, H r~>.
 eig_status rmm_dots2(const double* xt, const void* rt, const void* hrt, int mp, int64_t n, eig_dtype vt, double* part,
                      int* nparts, cudaStream_t st);

@@ -508,7 +508,9 @@ eig_status run_rmmdiis(Ctx& c, const double* X0, int maxiter, int* iters, bool* 
     int np = 0;
     EIG_TRY(rmm_combine(xh, rh, thh, alpha, win, thh + newest * mp, active, mp, n, vt, xt, hxt, rt, part, &np, c.st));
     EIG_TRY(reduce_partials(part, np, mp * 5, sums, c.st));
-    if (c.o.rmm_precond) EIG_TRY(jacobi_block(rt, thh + newest * mp, h->plan.diag.as<double>(), c.o.precond_floor, mp, n, vt, c.st));
+    if (c.o.rmm_precond)
+      EIG_TRY(rmm_precond_resid(xt, hxt, sums, active, h->plan.diag.as<double>(), c.o.precond_floor, mp, n, vt, rt,
+                                c.st));
     int nact = 0;
     for (int j = 0; j < mp; ++j) nact += act[j];
     EIG_TRY(c.spmm(rt, hrt, mp, vt, nact));
@@ -662,7 +664,14 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
   }
   auto front_then_rmm = [&](eig_method front) -> eig_status {
     std::vector<double> prev;
+    double best_rel = INFINITY;
     auto stop = [&](int it, const double* th, const double* rel) -> int {
+      double mxr = 0.0;
+      for (int j = 0; j < nev; ++j) mxr = std::max(mxr, rel[j]);
+      // the front has become unstable (Sec. 2.8: LOBPCG near convergence): residuals climbing
+      // well above their best -> hand over to RMM-DIIS now
+      if (best_rel < 1e-3 && mxr > 4.0 * best_rel) return 5;
+      best_rel = std::min(best_rel, mxr);
       double tau = INFINITY;
       if (!prev.empty()) {
         double s2 = 0.0;

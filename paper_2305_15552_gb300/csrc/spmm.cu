@@ -126,7 +126,7 @@ eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, in
   if (H->val_type != EIG_F32 && H->val_type != EIG_F64 && H->val_type != EIG_BF16) return EIG_EINVAL;
   if (H->n > INT32_MAX) return EIG_EUNSUPPORTED;  // int32 column indices
   if (R == 0) R = 256;
-  if (C == 0) C = std::min(128, R);
+  if (C == 0) C = std::min(64, R);
   if (R % 32 || C % 32 || R > 512 || C > R || R % C) return EIG_EINVAL;
   P->n = H->n; P->nnz = H->nnz; P->R = R; P->C = C; P->val_type = H->val_type;
   const int64_t n = H->n, nnz = H->nnz;
@@ -244,6 +244,7 @@ eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, in
     EIG_CUDA_TRY(cudaMemcpyAsync(P->sched_cb.p, h_sched_cb.data(), P->n_sched * 4, cudaMemcpyHostToDevice, st));
   if (s) EIG_CUDA_TRY(cudaMemcpyAsync(P->sched_slot.p, h_sched_slot.data(), s * 4, cudaMemcpyHostToDevice, st));
   EIG_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
+  if (C <= 256) EIG_TRY(spmm_plan_build_tiled(P, 2048, st));
   return EIG_OK;
 }
 
@@ -427,8 +428,35 @@ static eig_status launch_rowblock(SpmmPlan* P, const T* X, T* Y, T* Z, size_t sm
   return EIG_OK;
 }
 
+template <typename T, int NB>
+eig_status transpose_reduce_launch(SpmmPlan* P, const T* Z, T* Y, cudaStream_t st) {
+  if (P->n_sched) {
+    k_spmm_transpose_reduce<T, NB><<<(unsigned)P->n_sched, 256, 0, st>>>(
+        P->n, P->C, P->sched_ptr.as<int64_t>(), P->sched_cb.as<int32_t>(), P->sched_slot.as<int32_t>(), Z, Y);
+    EIG_LAUNCH_CHECK("k_spmm_transpose_reduce");
+  }
+  return EIG_OK;
+}
+#define EIG_TR_INST(T)                                                                   \
+  template eig_status transpose_reduce_launch<T, 1>(SpmmPlan*, const T*, T*, cudaStream_t);  \
+  template eig_status transpose_reduce_launch<T, 2>(SpmmPlan*, const T*, T*, cudaStream_t);  \
+  template eig_status transpose_reduce_launch<T, 4>(SpmmPlan*, const T*, T*, cudaStream_t);  \
+  template eig_status transpose_reduce_launch<T, 8>(SpmmPlan*, const T*, T*, cudaStream_t);  \
+  template eig_status transpose_reduce_launch<T, 16>(SpmmPlan*, const T*, T*, cudaStream_t); \
+  template eig_status transpose_reduce_launch<T, 32>(SpmmPlan*, const T*, T*, cudaStream_t);
+EIG_TR_INST(float)
+EIG_TR_INST(double)
+
+template <typename T, typename V, int NB> eig_status tiled_launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st);
+
 template <typename T, typename V, int NB>
 static eig_status launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st) {
+  if (P->tiled) {
+    // the tile-contiguous kernel; when its stages do not fit in shared memory (wide FP64
+    // blocks) the CSR kernel below computes the same product
+    const eig_status s = tiled_launch<T, V, NB>(P, X, Y, Z, st);
+    if (s != EIG_EUNSUPPORTED) return s;
+  }
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -439,12 +467,7 @@ static eig_status launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st) {
   } else {
     return EIG_EUNSUPPORTED;
   }
-  if (P->n_sched) {
-    k_spmm_transpose_reduce<T, NB><<<(unsigned)P->n_sched, 256, 0, st>>>(
-        P->n, P->C, P->sched_ptr.as<int64_t>(), P->sched_cb.as<int32_t>(), P->sched_slot.as<int32_t>(), Z, Y);
-    EIG_LAUNCH_CHECK("k_spmm_transpose_reduce");
-  }
-  return EIG_OK;
+  return transpose_reduce_launch<T, NB>(P, Z, Y, st);
 }
 
 template <typename T, typename V>

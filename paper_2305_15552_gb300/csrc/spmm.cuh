@@ -4,6 +4,20 @@
 
 namespace eig {
 
+// One chunk of a tile (row block I, column block J): rows [ra, rb) of the row block, entries
+// [ent_off, ent_off + nent) of the tiled arrays (nent_pad = nent rounded up to 16), row offsets
+// trp[rp_off .. rp_off + rb - ra] relative to ent_off.
+struct TileChunk {
+  int64_t ent_off;
+  int32_t nent_pad;
+  int32_t J;
+  int32_t rp_off;
+  int16_t ra, rb;
+  int32_t slot;    // scratch slot of the tile's transposed part, -1 for a tile inside the row block
+  int32_t flags;   // bit 0: first chunk of its tile, bit 1: last chunk of its tile
+};
+static_assert(sizeof(TileChunk) == 32, "TileChunk layout");
+
 struct SpmmPlan {
   int64_t n = 0, nnz = 0;
   int R = 256, C = 128;                 // row block / column block sizes
@@ -25,11 +39,24 @@ struct SpmmPlan {
   DevBuf sched_slot;   // int32[n_slots]
   int64_t n_sched = 0;
   DevBuf diag;         // float64[n]: H_ii (used by the Jacobi preconditioner)
+  // tile-contiguous copy of H (built by default): chunks of whole tile rows, each chunk's entries
+  // contiguous (uint8 column within the tile + value), 16-byte aligned for bulk copies
+  bool tiled = false;
+  int cap = 0;                 // entries per chunk at most (multiple of 16)
+  int64_t n_chunks = 0, tiled_entries = 0, tiled_rp = 0;
+  DevBuf chunk_ptr;            // int64[nRB+1]
+  DevBuf chunks;               // TileChunk[n_chunks]
+  DevBuf tcol;                 // uint8[tiled_entries]
+  DevBuf tval;                 // value type [tiled_entries]
+  DevBuf trp;                  // uint16 row offsets within chunks
+  DevBuf err;                  // int: device-side error flags (bounded waits that gave up)
   DevBuf scratch;      // transposed partial products, n_slots * C * nb * sizeof(T)
   double algorithmic_bytes(int nb, size_t vec_bytes) const;
 };
 
 eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, int copy, cudaStream_t st);
+// Builds the tile-contiguous copy (called by spmm_plan_build).
+eig_status spmm_plan_build_tiled(SpmmPlan* P, int cap, cudaStream_t st);
 eig_status spmm_run(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, cudaStream_t st);
 // Scratch bytes spmm_run needs for (nb, vec type); caller-provided scratch variant below.
 size_t spmm_scratch_bytes(const SpmmPlan* P, int nb, eig_dtype vt);

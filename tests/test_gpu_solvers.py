@@ -162,3 +162,30 @@ def test_lobpcg_trace_monotone(H3000):
     th = tr[:, 2:7]
     assert np.all(np.diff(th, axis=0) <= 1e-10 * np.abs(th[1:]))
     assert np.all(th >= lam[:5] - 1e-10)
+
+
+@pytest.mark.parametrize("vt", ["f32", "f64"])
+def test_hybrid_preconditioned_rmmdiis(H3000f, vt):
+    """RMM-DIIS with the Jacobi-preconditioned correction W = (x~, K^{-1} r~)."""
+    H, lam = H3000f
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type=vt, rmm_precond=1)
+    assert rc == 0, st
+    check_result(H, S, lam[:5])
+
+
+def test_rmmdiis_preconditioned_matches_oracle_step_count():
+    """Same start and method: the GPU converges to the oracle's eigenvalues and needs no more
+    batched RMM-DIIS iterations than the oracle (up to slack: the trajectories differ in rounding,
+    and this seed has a degenerate pair)."""
+    H = ci_matrix(3000, 100, 64, seed=2, storage="f64")
+    lam, Z = O.lowest_eigpairs(O.to_dense(H), 5)
+    X0 = Z + 1e-4 * random_block(H.n, 5, 5)
+    ref = O.rmmdiis(H, X0, tol=1e-8, maxiter=300, s_max=10, precond="jacobi")
+    assert ref.converged
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("rmmdiis", X0=X0, vec_type="f64", s_max=10, rmm_precond=1, tol=1e-8, maxiter=300)
+    assert rc == 0, st
+    assert st["iterations_rmm"] <= 1.5 * ref.iterations + 5
+    th, X, rel = S.ritz()
+    np.testing.assert_allclose(th, lam, rtol=1e-10)
