@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rmm-precond", type=int, default=1, choices=[0, 1],
+                    help="Jacobi-preconditioned RMM-DIIS corrections after the switch")
     return ap.parse_args()
 
 
@@ -201,7 +203,8 @@ def run_reference(args, ws, rank):
     n00 = max(args.nb * 4, n0 // 10)
     Z00 = O.lobpcg(principal_submatrix(H0, n00), np.random.default_rng(1).standard_normal((n00, args.nb)),
                    args.nb, tol=1e-4, maxiter=200).X
-    ref0 = O.hybrid(H0, pad_rows(Z00, n0), args.nev, tol=args.tol, U=U0, rmm_maxiter=300)
+    ref0 = O.hybrid(H0, pad_rows(Z00, n0), args.nev, tol=args.tol, U=U0, rmm_maxiter=300,
+                    rmm_precond="jacobi" if args.rmm_precond else "none")
     it_f, it_r = ref0.extra["front"].iterations, (ref0.extra["rmm"].iterations if ref0.extra["rmm"] else 0)
     X = np.random.default_rng(2).standard_normal((H.n, args.nb))
     times = []
@@ -226,7 +229,8 @@ def run_reference(args, ws, rank):
 
 
 def workload_config(args, H):
-    return {"workload": (f"hybrid LOBPCG->RMM-DIIS, n={H.n:,}, ~{args.nnz_per_row:g} nnz/row, "
+    rmm = "Jacobi-preconditioned RMM-DIIS" if args.rmm_precond else "RMM-DIIS"
+    return {"workload": (f"hybrid LOBPCG->{rmm}, n={H.n:,}, ~{args.nnz_per_row:g} nnz/row, "
                          f"block pattern {args.block_pattern}, half-stored nnz={H.nnz:,}, "
                          f"{args.storage} values / {args.vec} vectors, n_ev={args.nev}, block {args.nb}, "
                          f"tol {args.tol:g}"),
@@ -250,7 +254,7 @@ def main():
     X0 = initial_guess(H, args, binding)
     X0d = torch.tensor(X0, device="cuda")
     S = binding.Solver(H, args.nev, args.nb)
-    opts = dict(vec_type=args.vec, tol=args.tol, timing=1, maxiter=500)
+    opts = dict(vec_type=args.vec, tol=args.tol, timing=1, maxiter=500, rmm_precond=args.rmm_precond)
     st_ = torch.cuda.current_stream()
     for _ in range(args.warmup):
         S.solve("hybrid", X0=X0d, **opts)
@@ -263,6 +267,7 @@ def main():
     stats = None
     launches0 = lib.eig_launch_count()
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps
         ev0.record(st_)
         for _ in range(args.steps):
             rc, stats = S.solve("hybrid", X0=X0d, **opts)
@@ -271,6 +276,7 @@ def main():
             spmm_calls += stats["spmm_timed"]
         ev1.record(st_)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = lib.eig_launch_count() - launches0
     barrier(ws)
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -285,7 +291,7 @@ def main():
         torch.cuda.synchronize()
         t = time.perf_counter()
         S2 = binding.Solver(H, args.nev, args.nb)
-        S2.solve("hybrid", X0=X0, vec_type=args.vec, tol=args.tol, maxiter=500)
+        S2.solve("hybrid", X0=X0, vec_type=args.vec, tol=args.tol, maxiter=500, rmm_precond=args.rmm_precond)
         S2.ritz()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t) * 1e3)

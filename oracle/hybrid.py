@@ -29,7 +29,8 @@ def switch_tau(theta_k, theta_km1):
 
 
 def hybrid(H, X0, nev, tol=1e-6, front="lobpcg", switch_res=None, switch_tau_tol=1e-7,
-           switch_after=None, front_maxiter=200, rmm_maxiter=200, s_max=10, precond="jacobi", U=None):
+           switch_after=None, front_maxiter=200, rmm_maxiter=200, s_max=10, precond="jacobi", U=None,
+           rmm_precond="none"):
     U = to_scipy_upper(H) if U is None else U
     state = dict(prev=None, taus=[], why=None)
 
@@ -61,7 +62,8 @@ def hybrid(H, X0, nev, tol=1e-6, front="lobpcg", switch_res=None, switch_tau_tol
         return EigResult(theta=fr.theta[:nev], X=fr.X[:, :nev], relres=fr.relres[:nev], converged=True,
                          iterations=fr.iterations, spmm=fr.spmm, spmv=fr.spmv, history=fr.history,
                          extra=dict(front=fr, rmm=None, switch=None, taus=state["taus"]))
-    rm = rmmdiis(H, fr.X[:, :nev], tol=tol, maxiter=rmm_maxiter, s_max=s_max, HX0=fr.HX[:, :nev], U=U)
+    rm = rmmdiis(H, fr.X[:, :nev], tol=tol, maxiter=rmm_maxiter, s_max=s_max, HX0=fr.HX[:, :nev], U=U,
+                 precond=rmm_precond)
     return EigResult(theta=rm.theta, X=rm.X, relres=rm.relres, converged=rm.converged,
                      iterations=fr.iterations + rm.iterations, spmm=fr.spmm + rm.spmm, spmv=fr.spmv + rm.spmv,
                      HX=rm.HX, history=fr.history + rm.history,
