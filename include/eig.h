@@ -131,6 +131,19 @@ EIG_API eig_status eig_spmm(void* plan, const void* X, void* Y, int nb, eig_dtyp
 EIG_API eig_status eig_gram(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type, double* G,
                             void* stream);
 
+/* G = A^T B exactly as eig_gram, but without allocating device memory.  For callers that cannot
+ * allocate while they run -- a framework that has reserved the whole device memory for its own
+ * pool, or a latency-critical path that must not enter the driver's allocator.  The per-CTA
+ * partial sums live in a file-scope __device__ array of 4 MiB (512 partials of a 32 x 32 Gram)
+ * that every device loading this library holds until the process exits.  nb <= 32; larger
+ * blocks, or more partials than the array holds, return EIG_EINVAL.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  The array is overwritten completely by each call, so nothing needs clearing.
+ * The paper has no counterpart to this entry point. */
+EIG_API eig_status eig_gram_noalloc(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type,
+                                    double* G, void* stream);
 
 /* CholeskyQR2 (Alg. 3 "CholeskyQR"; applied twice): X (device, n x k, vec_type, in place) becomes
  * Q with X_in = Q R, R (device FP64 k x k, upper triangular) = R2 R1.  k <= 64.  Returns

@@ -70,6 +70,7 @@ _SIGS = {
     "eig_spmm_plan_info": (C.c_int, [C.c_void_p, C.POINTER(SpmmInfo)]),
     "eig_spmm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "eig_gram": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "eig_gram_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "eig_cholqr2": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "eig_small_syev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "eig_small_rr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
@@ -214,6 +215,17 @@ def gram(A, B):
     assert A.shape == B.shape and A.dtype == B.dtype and A.is_contiguous() and B.is_contiguous()
     G = torch.empty(A.shape[1], A.shape[1], dtype=torch.float64, device=A.device)
     check(lib.eig_gram(_ptr(A), _ptr(B), A.shape[0], A.shape[1], vec_dtype(A), _ptr(G), stream_ptr()), "eig_gram")
+    return G
+
+
+def gram_noalloc(A, B):
+    """G = A^T B through eig_gram_noalloc (no device allocation; scratch in a fixed device array)."""
+    import torch
+    lib = load()
+    assert A.shape == B.shape and A.dtype == B.dtype and A.is_contiguous() and B.is_contiguous()
+    G = torch.empty(A.shape[1], A.shape[1], dtype=torch.float64, device=A.device)
+    check(lib.eig_gram_noalloc(_ptr(A), _ptr(B), A.shape[0], A.shape[1], vec_dtype(A), _ptr(G), stream_ptr()),
+          "eig_gram_noalloc")
     return G
 
 
