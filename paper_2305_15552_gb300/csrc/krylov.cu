@@ -474,6 +474,7 @@ eig_status run_block_lanczos(Ctx& c, const double* X0, int x0c, int maxiter, con
     EIG_LAUNCH_CHECK("k_put_blocks");
     {
       k_negate_stack<<<4, 256, 0, c.st>>>(Cc, i + 1, nb, M);
+      EIG_LAUNCH_CHECK("k_negate_stack");
       BlockList in;
       in.n = i + 2;
       for (int b = 0; b <= i; ++b) in.p[b] = V[b];
@@ -481,6 +482,7 @@ eig_status run_block_lanczos(Ctx& c, const double* X0, int x0c, int maxiter, con
       EIG_TRY(block_apply(in, nb, M, nb, W, 0.0, n, vt, c.st));
       EIG_TRY(basis_gram(c, V.data(), i + 1, W, nb, vt, Cc, gpart));
       k_negate_stack<<<4, 256, 0, c.st>>>(Cc, i + 1, nb, M);
+      EIG_LAUNCH_CHECK("k_negate_stack");
       in.p[i + 1] = W;
       EIG_TRY(block_apply(in, nb, M, nb, HV, 0.0, n, vt, c.st));  // HV now holds W_i
     }

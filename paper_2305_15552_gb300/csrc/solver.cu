@@ -299,6 +299,7 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
     for (auto& r : mp.idx) for (int& v : r) v = -1;
     mp.idx[0][0] = 0;
     k_assemble<<<1, 256, 0, c.st>>>(Gp, mp, 1, nb, G);
+    EIG_LAUNCH_CHECK("k_assemble");
     mp.idx[0][0] = 1;
     k_assemble<<<1, 256, 0, c.st>>>(Gp, mp, 1, nb, A);
     EIG_LAUNCH_CHECK("k_assemble");
@@ -362,6 +363,7 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
     EIG_TRY(gram_multi(bl, pa, pb, np, nb, n, vt, Gp, gpart, c.st));
     int k = ns * nb;
     k_assemble<<<4, 256, 0, c.st>>>(Gp, mG, ns, nb, G);
+    EIG_LAUNCH_CHECK("k_assemble");
     k_assemble<<<4, 256, 0, c.st>>>(Gp, mA, ns, nb, A);
     EIG_LAUNCH_CHECK("k_assemble");
     EIG_TRY(small_rr(A, G, k, nb, piv_tol, theta, C, nullptr, rrwork, info, c.st));
@@ -376,6 +378,7 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
       for (int a = 0; a < 2; ++a)
         for (int b = a; b < 2; ++b) { g2.idx[a][b] = mG.idx[a][b]; a2.idx[a][b] = mA.idx[a][b]; }
       k_assemble<<<4, 256, 0, c.st>>>(Gp, g2, 2, nb, G);
+      EIG_LAUNCH_CHECK("k_assemble");
       k_assemble<<<4, 256, 0, c.st>>>(Gp, a2, 2, nb, A);
       EIG_LAUNCH_CHECK("k_assemble");
       EIG_TRY(small_rr(A, G, k, nb, piv_tol, theta, C, nullptr, rrwork, info, c.st));
