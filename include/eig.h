@@ -59,6 +59,21 @@ typedef enum {
   EIG_HYBRID = 5           /* Sec. 2.8 / Sec. 4: front method, then batched RMM-DIIS      */
 } eig_method;
 
+/* Device layout of an SpMM plan's copy of H (all compute the same Y = H X).
+ * MIRRORED: the plan expands the stored triangle into both triangles on the device (8-row
+ *   groups of 64-column tiles, 1-byte column indices); the kernel only gathers.  About twice
+ *   the matrix bytes of HALF, and the fastest on sm_103a.
+ * HALF: the stored triangle only (tile chunks); each stored entry is applied as both H_ij and
+ *   H_ji, the transposed half through per-tile scratch and a fixed-order reduction.
+ * CSR: the CSR copy itself, read by a reference kernel (no tiled copy is built).
+ * AUTO: MIRRORED when the device has room for it while it is built, else HALF. */
+typedef enum {
+  EIG_LAYOUT_AUTO = 0,
+  EIG_LAYOUT_MIRRORED = 1,
+  EIG_LAYOUT_HALF = 2,
+  EIG_LAYOUT_CSR = 3
+} eig_layout;
+
 /* Upper triangle (incl. diagonal) of a symmetric n x n matrix, CSR.
  * rowptr: int64[n+1], rowptr[0] = 0, non-decreasing; col: int32[nnz], within a row strictly
  * increasing and >= the row index (upper triangle); val: nnz values of val_type
@@ -97,10 +112,15 @@ EIG_API int64_t eig_launch_count(void);
  * copy = 1) and builds the tile lists and the transpose schedule of the atomic-free
  * scatter: rows are grouped in row blocks of `row_block` rows (multiple of 32, <= 512),
  * columns in column blocks of `col_block` columns (multiple of 32, <= row_block, dividing
- * row_block).  0 selects defaults (256, 128).  When copy = 0 and H is on the device the
- * plan keeps H's pointers, which must then outlive the plan.
+ * row_block).  0 selects defaults (256, 64); the mirrored layout needs exactly (256, 64).
+ * `layout` is an eig_layout; the layout actually built is reported by eig_spmm_plan_info
+ * (AUTO, or MIRRORED with other block sizes, falls back to HALF).  When copy = 0 and H is on
+ * the device the plan keeps H's pointers, which must then outlive the plan.
  * Errors: EIG_EINVAL if the CSR is malformed (checked on device: sortedness, col >= row,
- * col < n), EIG_ENOMEM, EIG_ECUDA. */
+ * col < n) or layout is unknown, EIG_ENOMEM, EIG_ECUDA. */
+EIG_API eig_status eig_spmm_plan_create_ex(const eig_csr_upper* H, int row_block, int col_block, int layout,
+                                           int copy, void* stream, void** plan);
+/* eig_spmm_plan_create_ex with layout = EIG_LAYOUT_AUTO. */
 EIG_API eig_status eig_spmm_plan_create(const eig_csr_upper* H, int row_block, int col_block, int copy,
                                 void* stream, void** plan);
 EIG_API void eig_spmm_plan_destroy(void* plan);
@@ -113,11 +133,15 @@ typedef struct {
   int64_t n_slots;          /* tiles whose transposed part goes through scratch            */
   int64_t scratch_bytes_per_col;  /* scratch bytes per vector column per byte of element    */
   eig_dtype val_type;
+  int layout;               /* eig_layout the kernels run on                               */
+  int64_t layout_entries;   /* entries the layout's kernel streams per product (with padding) */
+  int64_t device_bytes;     /* device bytes of the plan's copies of H                      */
 } eig_spmm_info;
 EIG_API eig_status eig_spmm_plan_info(const void* plan, eig_spmm_info* info);
 
 /* Y = H X.  X, Y: device, row-major n x nb, element type vec_type (EIG_F32 or EIG_F64),
- * nb in {1, 2, 4, 8, 16, 32}.  X and Y must not overlap.  Scratch for the transposed
+ * nb in {1, 2, 4, 8, 16, 32}, both aligned to min(16, nb * element size) bytes (EIG_EINVAL
+ * otherwise).  X and Y must not overlap.  Scratch for the transposed
  * partial products is owned by the plan (grown on demand; the first call for a given
  * (nb, vec_type) may allocate).  Deterministic: results are bitwise reproducible.
  * Supported (matrix, vector) types: (F32,F32), (F64,F64), (BF16,F32), (F32,F64). */
@@ -245,6 +269,8 @@ EIG_API void eig_default_opts(eig_opts* o);
  * SpMM plan is built (see eig_spmm_plan_create).  One handle serves one stream at a time.
  * Errors: EIG_EINVAL (n_ev < 1, n_ev > block, block > 32, n_ev > n, malformed CSR). */
 EIG_API eig_status eig_create(const eig_csr_upper* H, int n_ev, int block, void** handle);
+/* eig_create with the SpMM plan's device layout chosen explicitly (an eig_layout). */
+EIG_API eig_status eig_create_ex(const eig_csr_upper* H, int n_ev, int block, int layout, void** handle);
 EIG_API void eig_destroy(void* handle);
 
 /* Runs a method (opts NULL = defaults).  Returns EIG_OK when every pair met opts->tol,

@@ -38,7 +38,8 @@ class CsrUpper(C.Structure):
 class SpmmInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_block", C.c_int), ("col_block", C.c_int),
                 ("n_row_blocks", C.c_int64), ("n_col_blocks", C.c_int64), ("n_tiles", C.c_int64),
-                ("n_slots", C.c_int64), ("scratch_bytes_per_col", C.c_int64), ("val_type", C.c_int)]
+                ("n_slots", C.c_int64), ("scratch_bytes_per_col", C.c_int64), ("val_type", C.c_int),
+                ("layout", C.c_int), ("layout_entries", C.c_int64), ("device_bytes", C.c_int64)]
 
 
 class Opts(C.Structure):
@@ -67,6 +68,8 @@ _SIGS = {
     "eig_spmm_plan_create": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_void_p,
                                        C.POINTER(C.c_void_p)]),
     "eig_spmm_plan_destroy": (None, [C.c_void_p]),
+    "eig_spmm_plan_create_ex": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                          C.POINTER(C.c_void_p)]),
     "eig_spmm_plan_info": (C.c_int, [C.c_void_p, C.POINTER(SpmmInfo)]),
     "eig_spmm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "eig_gram": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
@@ -80,6 +83,7 @@ _SIGS = {
                                C.c_void_p]),
     "eig_default_opts": (None, [C.POINTER(Opts)]),
     "eig_create": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "eig_create_ex": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     "eig_destroy": (None, [C.c_void_p]),
     "eig_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Opts), C.POINTER(Stats)]),
     "eig_ritz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -157,10 +161,18 @@ def csr_struct(rowptr, col, val, storage, n, on_device):
     return s
 
 
+LAYOUTS = {"auto": 0, "mirrored": 1, "half": 2, "csr": 3}
+
+
+def layout_code(layout):
+    """eig_layout value of a layout name (or pass-through of an int)."""
+    return LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+
+
 class SpmmPlan:
     """eig_spmm_plan_create / eig_spmm / eig_spmm_plan_destroy."""
 
-    def __init__(self, H, row_block=0, col_block=0, device_arrays=None, copy=True):
+    def __init__(self, H, row_block=0, col_block=0, device_arrays=None, copy=True, layout="auto"):
         lib = load()
         self._keep = None
         if device_arrays is not None:
@@ -174,8 +186,8 @@ class SpmmPlan:
             st = csr_struct(rp, cl, vl, H.storage, H.n, False)
         self.n = H.n
         h = C.c_void_p()
-        check(lib.eig_spmm_plan_create(C.byref(st), int(row_block), int(col_block), 1 if copy else 0,
-                                       stream_ptr(), C.byref(h)), "eig_spmm_plan_create")
+        check(lib.eig_spmm_plan_create_ex(C.byref(st), int(row_block), int(col_block), layout_code(layout),
+                                          1 if copy else 0, stream_ptr(), C.byref(h)), "eig_spmm_plan_create_ex")
         self._h = h
         self._lib = lib
 
@@ -288,13 +300,14 @@ def rmm_diis(B, slots, active):
 class Solver:
     """eig_create / eig_solve / eig_ritz / eig_destroy."""
 
-    def __init__(self, H, n_ev, block):
+    def __init__(self, H, n_ev, block, layout="auto"):
         import numpy as np
         self._lib = lib = load()
         rp, cl, vl = (np.ascontiguousarray(H.rowptr), np.ascontiguousarray(H.col), np.ascontiguousarray(H.val))
         st = csr_struct(rp, cl, vl, H.storage, H.n, False)
         h = C.c_void_p()
-        check(lib.eig_create(C.byref(st), int(n_ev), int(block), C.byref(h)), "eig_create")
+        check(lib.eig_create_ex(C.byref(st), int(n_ev), int(block), layout_code(layout), C.byref(h)),
+              "eig_create_ex")
         self._h = h
         self.n, self.n_ev = H.n, n_ev
 

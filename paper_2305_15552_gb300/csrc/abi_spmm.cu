@@ -38,11 +38,17 @@ int64_t eig_launch_count(void) { return eig::g_launches.load(std::memory_order_r
 
 eig_status eig_spmm_plan_create(const eig_csr_upper* H, int row_block, int col_block, int copy, void* stream,
                                 void** plan) {
+  return eig_spmm_plan_create_ex(H, row_block, col_block, EIG_LAYOUT_AUTO, copy, stream, plan);
+}
+
+eig_status eig_spmm_plan_create_ex(const eig_csr_upper* H, int row_block, int col_block, int layout, int copy,
+                                   void* stream, void** plan) {
   if (!plan) return EIG_EINVAL;
   *plan = nullptr;
+  if (layout < EIG_LAYOUT_AUTO || layout > EIG_LAYOUT_CSR) return EIG_EINVAL;
   eig::SpmmPlan* P = new (std::nothrow) eig::SpmmPlan();
   if (!P) return EIG_ENOMEM;
-  eig_status s = eig::spmm_plan_build(P, H, row_block, col_block, copy, eig::as_stream(stream));
+  eig_status s = eig::spmm_plan_build(P, H, row_block, col_block, layout, copy, eig::as_stream(stream));
   if (s != EIG_OK) {
     cudaStreamSynchronize(eig::as_stream(stream));
     delete P;
@@ -71,6 +77,18 @@ eig_status eig_spmm_plan_info(const void* plan, eig_spmm_info* info) {
   info->n_slots = P->n_slots;
   info->scratch_bytes_per_col = P->n_slots * (int64_t)P->C;
   info->val_type = P->val_type;
+  info->layout = P->layout;
+  const int64_t vb = (int64_t)eig::dtype_size(P->val_type);
+  if (P->layout == EIG_LAYOUT_MIRRORED) {
+    info->layout_entries = P->m_slots;
+    info->device_bytes = P->m_slots * (1 + vb);
+  } else if (P->layout == EIG_LAYOUT_HALF) {
+    info->layout_entries = P->tiled_entries;
+    info->device_bytes = P->tiled_entries * (1 + vb) + P->tiled_rp * 2;
+  } else {
+    info->layout_entries = P->nnz;
+    info->device_bytes = P->nnz * (4 + vb) + (P->n + 1) * 8;
+  }
   return EIG_OK;
 }
 

@@ -607,16 +607,21 @@ void eig_default_opts(eig_opts* o) {
 }
 
 eig_status eig_create(const eig_csr_upper* H, int n_ev, int block, void** handle) {
+  return eig_create_ex(H, n_ev, block, EIG_LAYOUT_AUTO, handle);
+}
+
+eig_status eig_create_ex(const eig_csr_upper* H, int n_ev, int block, int layout, void** handle) {
   if (!handle || !H) return EIG_EINVAL;
   *handle = nullptr;
   if (n_ev < 1 || block < n_ev || block > 32 || n_ev > H->n) return EIG_EINVAL;
+  if (layout < EIG_LAYOUT_AUTO || layout > EIG_LAYOUT_CSR) return EIG_EINVAL;
   Handle* h = new (std::nothrow) Handle();
   if (!h) return EIG_ENOMEM;
   h->n = H->n;
   h->n_ev = n_ev;
   h->nb = next_pow2(block);
   if (h->nb > H->n) h->nb = std::max(n_ev, (int)H->n);
-  eig_status s = spmm_plan_build(&h->plan, H, 0, 0, 1, nullptr);
+  eig_status s = spmm_plan_build(&h->plan, H, 0, 0, layout, 1, nullptr);
   if (s != EIG_OK) {
     cudaDeviceSynchronize();
     delete h;

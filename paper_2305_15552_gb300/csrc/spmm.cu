@@ -116,12 +116,48 @@ __global__ void k_tile_fill(int64_t nRB, int64_t words_per_rb, const unsigned* _
   }
 }
 
+eig_status build_tile_lists(int64_t n, int R, int C, const int64_t* rowptr, const int32_t* col, cudaStream_t st,
+                            DevBuf& tile_ptr, DevBuf& tile_col, std::vector<int64_t>& h_ptr,
+                            std::vector<int32_t>& h_col) {
+  const int64_t nRB = (n + R - 1) / R, nCB = (n + C - 1) / C;
+  const int64_t wpr = (nCB + 31) / 32;
+  const int tb = 256;
+  const int64_t gb = (n + tb - 1) / tb;
+  DevBuf bitmap;
+  EIG_TRY(bitmap.reserve(nRB * wpr * 4));
+  EIG_CUDA_TRY(cudaMemsetAsync(bitmap.p, 0, nRB * wpr * 4, st));
+  k_tile_bitmap<<<(unsigned)gb, tb, 0, st>>>(n, R, C, wpr, rowptr, col, bitmap.as<unsigned>());
+  EIG_LAUNCH_CHECK("k_tile_bitmap");
+  DevBuf cnt;
+  EIG_TRY(cnt.reserve(nRB * 8));
+  const int64_t wb = (nRB * 32 + tb - 1) / tb;
+  k_tile_count<<<(unsigned)wb, tb, 0, st>>>(nRB, wpr, bitmap.as<unsigned>(), cnt.as<int64_t>());
+  EIG_LAUNCH_CHECK("k_tile_count");
+  std::vector<int64_t> h_cnt(nRB);
+  h_ptr.assign(nRB + 1, 0);
+  EIG_CUDA_TRY(cudaMemcpyAsync(h_cnt.data(), cnt.p, nRB * 8, cudaMemcpyDeviceToHost, st));
+  EIG_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int64_t I = 0; I < nRB; ++I) h_ptr[I + 1] = h_ptr[I] + h_cnt[I];
+  const int64_t nt = h_ptr[nRB];
+  EIG_TRY(tile_ptr.reserve((nRB + 1) * 8));
+  EIG_TRY(tile_col.reserve(std::max<int64_t>(nt, 1) * 4));
+  EIG_CUDA_TRY(cudaMemcpyAsync(tile_ptr.p, h_ptr.data(), (nRB + 1) * 8, cudaMemcpyHostToDevice, st));
+  k_tile_fill<<<(unsigned)wb, tb, 0, st>>>(nRB, wpr, bitmap.as<unsigned>(), tile_ptr.as<int64_t>(),
+                                          tile_col.as<int32_t>());
+  EIG_LAUNCH_CHECK("k_tile_fill");
+  h_col.assign(nt, 0);
+  if (nt) EIG_CUDA_TRY(cudaMemcpyAsync(h_col.data(), tile_col.p, nt * 4, cudaMemcpyDeviceToHost, st));
+  EIG_CUDA_TRY(cudaStreamSynchronize(st));
+  return EIG_OK;
+}
+
 double SpmmPlan::algorithmic_bytes(int nb, size_t vb) const {
   // one read of the stored triangle (values + int32 columns) and of rowptr, X read and Y written once
   return double(nnz) * (dtype_size(val_type) + 4.0) + 8.0 * double(n + 1) + 2.0 * double(n) * nb * double(vb);
 }
 
-eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, int copy, cudaStream_t st) {
+eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, int layout, int copy,
+                           cudaStream_t st) {
   if (!H || H->n <= 0 || H->nnz < 0 || !H->rowptr || (!H->col && H->nnz) || (!H->val && H->nnz)) return EIG_EINVAL;
   if (H->val_type != EIG_F32 && H->val_type != EIG_F64 && H->val_type != EIG_BF16) return EIG_EINVAL;
   if (H->n > INT32_MAX) return EIG_EUNSUPPORTED;  // int32 column indices
@@ -173,32 +209,10 @@ eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, in
   // tile bitmap -> per-row-block tile lists
   P->nRB = (n + R - 1) / R;
   P->nCB = (n + C - 1) / C;
-  const int64_t wpr = (P->nCB + 31) / 32;
-  DevBuf bitmap;
-  EIG_TRY(bitmap.reserve(P->nRB * wpr * 4));
-  EIG_CUDA_TRY(cudaMemsetAsync(bitmap.p, 0, P->nRB * wpr * 4, st));
-  k_tile_bitmap<<<(unsigned)gb, tb, 0, st>>>(n, R, C, wpr, P->rowptr, P->col, bitmap.as<unsigned>());
-  EIG_LAUNCH_CHECK("k_tile_bitmap");
-  DevBuf cnt;
-  EIG_TRY(cnt.reserve(P->nRB * 8));
-  const int64_t wb = (P->nRB * 32 + tb - 1) / tb;
-  k_tile_count<<<(unsigned)wb, tb, 0, st>>>(P->nRB, wpr, bitmap.as<unsigned>(), cnt.as<int64_t>());
-  EIG_LAUNCH_CHECK("k_tile_count");
-  std::vector<int64_t> h_cnt(P->nRB), h_ptr(P->nRB + 1, 0);
-  EIG_CUDA_TRY(cudaMemcpyAsync(h_cnt.data(), cnt.p, P->nRB * 8, cudaMemcpyDeviceToHost, st));
-  EIG_CUDA_TRY(cudaStreamSynchronize(st));
-  for (int64_t I = 0; I < P->nRB; ++I) h_ptr[I + 1] = h_ptr[I] + h_cnt[I];
+  std::vector<int64_t> h_ptr;
+  std::vector<int32_t> h_col;
+  EIG_TRY(build_tile_lists(n, R, C, P->rowptr, P->col, st, P->tile_ptr, P->tile_col, h_ptr, h_col));
   P->n_tiles = h_ptr[P->nRB];
-  EIG_TRY(P->tile_ptr.reserve((P->nRB + 1) * 8));
-  EIG_TRY(P->tile_col.reserve(std::max<int64_t>(P->n_tiles, 1) * 4));
-  EIG_CUDA_TRY(cudaMemcpyAsync(P->tile_ptr.p, h_ptr.data(), (P->nRB + 1) * 8, cudaMemcpyHostToDevice, st));
-  k_tile_fill<<<(unsigned)wb, tb, 0, st>>>(P->nRB, wpr, bitmap.as<unsigned>(), P->tile_ptr.as<int64_t>(),
-                                          P->tile_col.as<int32_t>());
-  EIG_LAUNCH_CHECK("k_tile_fill");
-  std::vector<int32_t> h_col(P->n_tiles);
-  if (P->n_tiles)
-    EIG_CUDA_TRY(cudaMemcpyAsync(h_col.data(), P->tile_col.p, P->n_tiles * 4, cudaMemcpyDeviceToHost, st));
-  EIG_CUDA_TRY(cudaStreamSynchronize(st));
   // slots for non-local tiles (column block outside the row block's own row range), and the
   // transpose schedule: a stable counting sort of the slots by column block.
   const int64_t cpr = R / C;  // column blocks per row block
@@ -243,8 +257,24 @@ eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, in
   if (P->n_sched)
     EIG_CUDA_TRY(cudaMemcpyAsync(P->sched_cb.p, h_sched_cb.data(), P->n_sched * 4, cudaMemcpyHostToDevice, st));
   if (s) EIG_CUDA_TRY(cudaMemcpyAsync(P->sched_slot.p, h_sched_slot.data(), s * 4, cudaMemcpyHostToDevice, st));
-  EIG_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
-  if (C <= 256) EIG_TRY(spmm_plan_build_tiled(P, 2048, st));
+  EIG_CUDA_TRY(cudaStreamSynchronize(st));
+  P->layout = EIG_LAYOUT_CSR;
+  if (layout == EIG_LAYOUT_CSR) return EIG_OK;
+  bool want_mirror = (layout == EIG_LAYOUT_MIRRORED || layout == EIG_LAYOUT_AUTO) && R == 256 && C == 64;
+  if (want_mirror && layout == EIG_LAYOUT_AUTO) {
+    size_t fr = 0, tot = 0;
+    EIG_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    want_mirror = mirror_bytes_estimate(P) < fr / 10 * 8;
+  }
+  if (want_mirror) {
+    EIG_TRY(spmm_plan_build_mirror(P, h_ptr, h_col, st));
+    P->layout = EIG_LAYOUT_MIRRORED;
+    return EIG_OK;
+  }
+  if (C <= 256) {
+    EIG_TRY(spmm_plan_build_tiled(P, 2048, st));
+    P->layout = EIG_LAYOUT_HALF;
+  }
   return EIG_OK;
 }
 
@@ -414,6 +444,7 @@ static size_t smem_bytes(const SpmmPlan* P, int warps) {
 }
 
 size_t spmm_scratch_bytes(const SpmmPlan* P, int nb, eig_dtype vt) {
+  if (P->mirrored) return 16;
   return (size_t)std::max<int64_t>(P->n_slots, 1) * P->C * nb * dtype_size(vt);
 }
 
@@ -448,9 +479,13 @@ EIG_TR_INST(float)
 EIG_TR_INST(double)
 
 template <typename T, typename V, int NB> eig_status tiled_launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st);
+template <typename T, typename V, int NB> eig_status mirror_launch(SpmmPlan* P, const T* X, T* Y, cudaStream_t st);
 
 template <typename T, typename V, int NB>
 static eig_status launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st) {
+  // gather-only kernel on the mirrored copy (its stages fit in shared memory for every
+  // supported shape; it needs no scratch)
+  if (P->mirrored) return mirror_launch<T, V, NB>(P, X, Y, st);
   if (P->tiled) {
     // the tile-contiguous kernel; when its stages do not fit in shared memory (wide FP64
     // blocks) the CSR kernel below computes the same product
@@ -486,6 +521,10 @@ static eig_status dispatch_nb(SpmmPlan* P, const T* X, T* Y, T* Z, int nb, cudaS
 eig_status spmm_run_with_scratch(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, void* scratch,
                                  cudaStream_t st) {
   if (!P || !X || !Y) return EIG_EINVAL;
+  if (vt != EIG_F32 && vt != EIG_F64) return EIG_EINVAL;
+  // every kernel moves X and Y rows in pieces of min(16, nb * element size) bytes
+  const uintptr_t align = (uintptr_t)std::min<size_t>(16, (size_t)nb * dtype_size(vt));
+  if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & (align - 1)) return EIG_EINVAL;
   if (vt == EIG_F32) {
     const float* x = static_cast<const float*>(X);
     float* y = static_cast<float*>(Y);

@@ -18,9 +18,21 @@ struct TileChunk {
 };
 static_assert(sizeof(TileChunk) == 32, "TileChunk layout");
 
+// One chunk of the mirrored layout: groups [g0, g1) of tile (row block, column block J), quads
+// [ent_off / 32, ent_off / 32 + nq) of the slot arrays.
+struct MirrorChunk {
+  int64_t ent_off;  // first slot (multiple of 32)
+  int32_t nq;       // quads in the chunk
+  int32_t J;
+  int32_t g0, g1;
+  int64_t pad;
+};
+static_assert(sizeof(MirrorChunk) == 32, "MirrorChunk layout");
+
 struct SpmmPlan {
   int64_t n = 0, nnz = 0;
-  int R = 256, C = 128;                 // row block / column block sizes
+  int R = 256, C = 64;                  // row block / column block sizes
+  int layout = EIG_LAYOUT_CSR;          // layout the kernels run on (eig_layout)
   int64_t nRB = 0, nCB = 0;
   eig_dtype val_type = EIG_F32;
   // matrix (owned when copied)
@@ -51,10 +63,30 @@ struct SpmmPlan {
   DevBuf trp;                  // uint16 row offsets within chunks
   DevBuf err;                  // int: device-side error flags (bounded waits that gave up)
   DevBuf scratch;      // transposed partial products, n_slots * C * nb * sizeof(T)
+  // mirrored copy of H (both triangles; gather-only kernel): per row block, chunks of 8-row
+  // group quads (32 slots of uint8 column in tile + value), padded slots have column 0xFF
+  bool mirrored = false;
+  int m_capq = 0;                    // quads per chunk at most
+  int64_t m_nchunks = 0, m_slots = 0, m_full_nnz = 0;
+  DevBuf m_chunk_ptr;                // int64[nRB+1]
+  DevBuf m_chunks;                   // MirrorChunk[m_nchunks]
+  DevBuf m_gq;                       // uint8[32 * m_nchunks]: quads of each group of a chunk
+  DevBuf m_col;                      // uint8[m_slots]
+  DevBuf m_val;                      // value type [m_slots]
   double algorithmic_bytes(int nb, size_t vec_bytes) const;
 };
 
-eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, int copy, cudaStream_t st);
+eig_status spmm_plan_build(SpmmPlan* P, const eig_csr_upper* H, int R, int C, int layout, int copy,
+                           cudaStream_t st);
+// Per row block of R rows, the ascending column blocks (of C) in which a sorted CSR has entries.
+eig_status build_tile_lists(int64_t n, int R, int C, const int64_t* rowptr, const int32_t* col, cudaStream_t st,
+                            DevBuf& tile_ptr, DevBuf& tile_col, std::vector<int64_t>& h_ptr,
+                            std::vector<int32_t>& h_col);
+// Builds the mirrored layout from the plan's CSR and tile lists (R = 256, C = 64 only).
+eig_status spmm_plan_build_mirror(SpmmPlan* P, const std::vector<int64_t>& h_tptr,
+                                  const std::vector<int32_t>& h_tcol, cudaStream_t st);
+// Device bytes the mirrored layout needs while it is built (estimate).
+size_t mirror_bytes_estimate(const SpmmPlan* P);
 // Builds the tile-contiguous copy (called by spmm_plan_build).
 eig_status spmm_plan_build_tiled(SpmmPlan* P, int cap, cudaStream_t st);
 eig_status spmm_run(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, cudaStream_t st);
