@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rmm-precond", type=int, default=1, choices=[0, 1],
                     help="Jacobi-preconditioned RMM-DIIS corrections after the switch")
+    ap.add_argument("--switch-res", type=float, default=1e-2,
+                    help="switch to RMM-DIIS once every wanted relative residual is below this")
+    ap.add_argument("--switch-tau", type=float, default=0.0,
+                    help="switch on the eigenvalue-change rule tau <= this (0: off)")
+    ap.add_argument("--layout", default="auto", choices=["auto", "mirrored", "half", "csr"],
+                    help="device layout of the SpMM plan")
     return ap.parse_args()
 
 
@@ -204,7 +210,9 @@ def run_reference(args, ws, rank):
     Z00 = O.lobpcg(principal_submatrix(H0, n00), np.random.default_rng(1).standard_normal((n00, args.nb)),
                    args.nb, tol=1e-4, maxiter=200).X
     ref0 = O.hybrid(H0, pad_rows(Z00, n0), args.nev, tol=args.tol, U=U0, rmm_maxiter=300,
-                    rmm_precond="jacobi" if args.rmm_precond else "none")
+                    rmm_precond="jacobi" if args.rmm_precond else "none",
+                    switch_res=args.switch_res if args.switch_res > 0 else None,
+                    switch_tau_tol=args.switch_tau if args.switch_tau > 0 else None)
     it_f, it_r = ref0.extra["front"].iterations, (ref0.extra["rmm"].iterations if ref0.extra["rmm"] else 0)
     X = np.random.default_rng(2).standard_normal((H.n, args.nb))
     times = []
@@ -228,14 +236,25 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+SPMM_KERNELS = {1: "k_spmm_mirror (mirrored tiles, gather only)",
+                2: "k_spmm_tiled + k_spmm_transpose_reduce (half-stored tiles)",
+                3: "k_spmm_rowblock + k_spmm_transpose_reduce (CSR)"}
+
+
 def workload_config(args, H):
     rmm = "Jacobi-preconditioned RMM-DIIS" if args.rmm_precond else "RMM-DIIS"
-    return {"workload": (f"hybrid LOBPCG->{rmm}, n={H.n:,}, ~{args.nnz_per_row:g} nnz/row, "
+    sw = []
+    if args.switch_res > 0:
+        sw.append(f"residual {args.switch_res:g}")
+    if args.switch_tau > 0:
+        sw.append(f"tau {args.switch_tau:g}")
+    return {"workload": (f"hybrid LOBPCG (to {' or '.join(sw)}) -> {rmm}, n={H.n:,}, ~{args.nnz_per_row:g} nnz/row, "
                          f"block pattern {args.block_pattern}, half-stored nnz={H.nnz:,}, "
                          f"{args.storage} values / {args.vec} vectors, n_ev={args.nev}, block {args.nb}, "
                          f"tol {args.tol:g}"),
             "n": H.n, "nnz_half": H.nnz, "n_ev": args.nev, "block": args.nb, "values": args.storage,
-            "vectors": args.vec, "l2": "inputs larger than L2 (matrix ~3.2 GB), no flush",
+            "vectors": args.vec, "layout": args.layout, "switch_res": args.switch_res,
+            "switch_tau": args.switch_tau, "l2": "inputs larger than L2 (matrix ~3.2 GB), no flush",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
@@ -253,8 +272,10 @@ def main():
     H, tgen = make_problem(args)
     X0 = initial_guess(H, args, binding)
     X0d = torch.tensor(X0, device="cuda")
-    S = binding.Solver(H, args.nev, args.nb)
-    opts = dict(vec_type=args.vec, tol=args.tol, timing=1, maxiter=500, rmm_precond=args.rmm_precond)
+    S = binding.Solver(H, args.nev, args.nb, layout=args.layout)
+    pinfo = S.spmm_info()
+    opts = dict(vec_type=args.vec, tol=args.tol, timing=1, maxiter=500, rmm_precond=args.rmm_precond,
+                switch_res=args.switch_res, switch_tau=args.switch_tau)
     st_ = torch.cuda.current_stream()
     for _ in range(args.warmup):
         S.solve("hybrid", X0=X0d, **opts)
@@ -290,8 +311,9 @@ def main():
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        S2 = binding.Solver(H, args.nev, args.nb)
-        S2.solve("hybrid", X0=X0, vec_type=args.vec, tol=args.tol, maxiter=500, rmm_precond=args.rmm_precond)
+        S2 = binding.Solver(H, args.nev, args.nb, layout=args.layout)
+        S2.solve("hybrid", X0=X0, vec_type=args.vec, tol=args.tol, maxiter=500, rmm_precond=args.rmm_precond,
+                 switch_res=args.switch_res, switch_tau=args.switch_tau)
         S2.ritz()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t) * 1e3)
@@ -307,7 +329,8 @@ def main():
         "config": workload_config(args, H),
         "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "symmetric SpMM (row-block pass + transpose-schedule reduce)",
+        "roofline": {"bound": "hbm", "kernel": SPMM_KERNELS.get(pinfo["layout"], "symmetric SpMM"),
+                     "layout_device_bytes": pinfo["device_bytes"],
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": spmm_bytes / max(spmm_calls, 1),

@@ -144,6 +144,9 @@ EIG_API eig_status eig_spmm_plan_info(const void* plan, eig_spmm_info* info);
  * otherwise).  X and Y must not overlap.  Scratch for the transposed
  * partial products is owned by the plan (grown on demand; the first call for a given
  * (nb, vec_type) may allocate).  Deterministic: results are bitwise reproducible.
+ * Arithmetic: FP32 vectors in FP32; FP64 vectors with FP64 values in FP64; FP64 vectors with
+ * FP32 values in the mirrored layout in double-float (exact FP32 products summed as two FP32
+ * words, ~2^-44 relative per step), which sm_103a runs at FP32 rate.
  * Supported (matrix, vector) types: (F32,F32), (F64,F64), (BF16,F32), (F32,F64). */
 EIG_API eig_status eig_spmm(void* plan, const void* X, void* Y, int nb, eig_dtype vec_type, void* stream);
 
@@ -271,6 +274,8 @@ EIG_API void eig_default_opts(eig_opts* o);
 EIG_API eig_status eig_create(const eig_csr_upper* H, int n_ev, int block, void** handle);
 /* eig_create with the SpMM plan's device layout chosen explicitly (an eig_layout). */
 EIG_API eig_status eig_create_ex(const eig_csr_upper* H, int n_ev, int block, int layout, void** handle);
+/* Description of the SpMM plan a solver handle built (layout, tiles, device bytes). */
+EIG_API eig_status eig_solver_spmm_info(const void* handle, eig_spmm_info* info);
 EIG_API void eig_destroy(void* handle);
 
 /* Runs a method (opts NULL = defaults).  Returns EIG_OK when every pair met opts->tol,

@@ -84,6 +84,7 @@ _SIGS = {
     "eig_default_opts": (None, [C.POINTER(Opts)]),
     "eig_create": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     "eig_create_ex": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "eig_solver_spmm_info": (C.c_int, [C.c_void_p, C.POINTER(SpmmInfo)]),
     "eig_destroy": (None, [C.c_void_p]),
     "eig_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Opts), C.POINTER(Stats)]),
     "eig_ritz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -310,6 +311,12 @@ class Solver:
               "eig_create_ex")
         self._h = h
         self.n, self.n_ev = H.n, n_ev
+
+    def spmm_info(self):
+        """eig_solver_spmm_info as a dict (layout, tiles, device bytes of the SpMM plan)."""
+        inf = SpmmInfo()
+        check(self._lib.eig_solver_spmm_info(self._h, C.byref(inf)), "eig_solver_spmm_info")
+        return {k: getattr(inf, k) for k, _ in SpmmInfo._fields_}
 
     def solve(self, method="hybrid", X0=None, **opts):
         """Runs a method; returns (status, stats dict).  X0: numpy (host) or torch (device) FP64

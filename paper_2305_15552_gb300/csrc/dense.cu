@@ -109,13 +109,17 @@ k_gram(BlockList blocks, PairList pairs, int nb, int64_t n, int64_t rows_per_cta
   }
 }
 
-// out[j] = sum over parts in fixed order
+// out[j] = sum over parts in fixed order: one warp per output, lane l adds parts l, l+32, ...,
+// then a fixed xor tree (bitwise reproducible, and the loads of a warp are independent).
 __global__ void k_reduce_partials(const double* __restrict__ part, int nparts, int m, double* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (j >= m) return;
   double s = 0.0;
-  for (int b = 0; b < nparts; ++b) s += part[(size_t)b * m + j];
-  out[j] = s;
+  for (int b = lane; b < nparts; b += 32) s += part[(size_t)b * m + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[j] = s;
 }
 
 static int gram_grid(int64_t n, int64_t* rows_per_cta) {
@@ -131,7 +135,7 @@ static int gram_grid(int64_t n, int64_t* rows_per_cta) {
 size_t gram_scratch_bytes(int npairs, int nb) { return (size_t)num_sms() * 2 * npairs * nb * nb * 8 + 256; }
 
 eig_status reduce_partials(const double* part, int nparts, int m, double* out, cudaStream_t st) {
-  k_reduce_partials<<<(m + 255) / 256, 256, 0, st>>>(part, nparts, m, out);
+  k_reduce_partials<<<(unsigned)(((int64_t)m * 32 + 255) / 256), 256, 0, st>>>(part, nparts, m, out);
   EIG_LAUNCH_CHECK("k_reduce_partials");
   return EIG_OK;
 }

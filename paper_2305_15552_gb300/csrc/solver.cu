@@ -631,6 +631,11 @@ eig_status eig_create_ex(const eig_csr_upper* H, int n_ev, int block, int layout
   return EIG_OK;
 }
 
+eig_status eig_solver_spmm_info(const void* handle, eig_spmm_info* info) {
+  if (!handle || !info) return EIG_EINVAL;
+  return eig_spmm_plan_info(&static_cast<const Handle*>(handle)->plan, info);
+}
+
 void eig_destroy(void* handle) {
   if (!handle) return;
   cudaDeviceSynchronize();

@@ -432,6 +432,90 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int j) {
   return r;
 }
 
+// Accumulation of y += v * x over one lane's EPL elements.
+//   Plain: X rows staged as T, fma in T.
+//   DF (FP64 vectors with FP32 or BF16 values): X rows staged as (hi, lo) FP32 pairs (same 8 bytes
+//   per element as FP64), each product taken exactly (hi part by an FMA-based two-product, lo part
+//   rounded) and summed in double-float (two-sum into hi, errors into lo): ~2^-44 relative per
+//   step, at FP32 instruction rate instead of the much slower FP64 pipe of sm_103a.
+template <bool DF, typename T, int EPL> struct MirrorAcc;
+template <typename T, int EPL> struct MirrorAcc<false, T, EPL> {
+  typedef T VT;   // value type in arithmetic
+  typedef Vec<T, EPL> XV;
+  Vec<T, EPL> y;
+  __device__ __forceinline__ void zero() { y.zero(); }
+  __device__ __forceinline__ static XV load(const unsigned char* p) {
+    return VecIO<T, EPL>::ld(reinterpret_cast<const T*>(p));
+  }
+  __device__ __forceinline__ void add(T v, const XV& x) {
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) y.v[e] = fma(v, x.v[e], y.v[e]);
+  }
+  __device__ __forceinline__ T get(int e) const { return y.v[e]; }
+  // staged form of one element
+  __device__ __forceinline__ static void stage(const T* src, unsigned char* dst) {
+    VecIO<T, EPL>::st(reinterpret_cast<T*>(dst), VecIO<T, EPL>::ld(src));
+  }
+  __device__ __forceinline__ static void stage_zero(unsigned char* dst) {
+    Vec<T, EPL> z;
+    z.zero();
+    VecIO<T, EPL>::st(reinterpret_cast<T*>(dst), z);
+  }
+};
+template <int EPL> struct MirrorAcc<true, double, EPL> {
+  typedef float VT;
+  struct XV { float h[EPL], l[EPL]; };
+  float hi[EPL], lo[EPL];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) hi[e] = lo[e] = 0.0f;
+  }
+  __device__ __forceinline__ static XV load(const unsigned char* p) {
+    XV x;
+    if (EPL == 2) {
+      const float4 a = *reinterpret_cast<const float4*>(p);
+      x.h[0] = a.x; x.l[0] = a.y; x.h[EPL - 1] = a.z; x.l[EPL - 1] = a.w;
+    } else {
+      const float2 a = *reinterpret_cast<const float2*>(p);
+      x.h[0] = a.x; x.l[0] = a.y;
+    }
+    return x;
+  }
+  __device__ __forceinline__ void add(float v, const XV& x) {
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const float p = v * x.h[e];
+      const float pe = fmaf(v, x.h[e], -p);          // v * x.h[e] = p + pe exactly
+      const float s = hi[e] + p;
+      const float bb = s - hi[e];
+      const float err = (hi[e] - (s - bb)) + (p - bb);  // hi + p = s + err exactly
+      hi[e] = s;
+      lo[e] = fmaf(v, x.l[e], lo[e] + (err + pe));
+    }
+  }
+  __device__ __forceinline__ double get(int e) const { return (double)hi[e] + (double)lo[e]; }
+  __device__ __forceinline__ static void stage(const double* src, unsigned char* dst) {
+    float* d = reinterpret_cast<float*>(dst);
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const double x = src[e];
+      const float h = __double2float_rn(x);
+      d[2 * e] = h;
+      d[2 * e + 1] = __double2float_rn(x - (double)h);
+    }
+  }
+  __device__ __forceinline__ static void stage_zero(unsigned char* dst) {
+    float* d = reinterpret_cast<float*>(dst);
+#pragma unroll
+    for (int e = 0; e < 2 * EPL; ++e) d[e] = 0.0f;
+  }
+};
+
+// Double-float accumulation applies to FP64 vectors with FP32 or BF16 values.
+template <typename T, typename V> struct MirrorDF { static constexpr bool value = false; };
+template <> struct MirrorDF<double, float> { static constexpr bool value = true; };
+template <> struct MirrorDF<double, uint16_t> { static constexpr bool value = true; };
+
 // Launch shape of the kernel for (T, NB).
 template <typename T, int NB> struct MirrorShape {
   typedef LaneShape<T, NB> S;
@@ -451,7 +535,7 @@ template <typename T, int NB> struct MirrorShape {
 };
 
 template <typename T, typename V, int NB>
-__global__ void __launch_bounds__(MirrorShape<T, NB>::WARPS * 32)
+__global__ void __launch_bounds__(MirrorShape<T, NB>::WARPS * 32, MirrorShape<T, NB>::WARPS == 8 ? 1 : 2)
 k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_bulk) {
   typedef MirrorShape<T, NB> Sh;
   constexpr int EPL = Sh::EPL, L = Sh::L, RPI = Sh::RPI, SB = Sh::SB, M = Sh::M, JJ = Sh::JJ;
@@ -459,6 +543,9 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
   constexpr int NT = WARPS * 32;
   static_assert(M * JJ == 4, "quad split");
   typedef typename ValLoad<V>::storage VS;
+  constexpr bool DF = MirrorDF<T, V>::value;
+  typedef MirrorAcc<DF, T, EPL> Acc;
+  typedef typename Acc::VT AT;
   extern __shared__ __align__(128) unsigned char smem[];
   const MirrorStage SL(a.capq, (int)sizeof(VS), RB);
   unsigned char* stage[2] = {smem, smem + SL.bytes};
@@ -474,7 +561,7 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
   const int64_t c0 = a.chunk_ptr[I], c1 = a.chunk_ptr[I + 1];
   const VS* mval = static_cast<const VS*>(a.mval);
 
-  Vec<T, EPL> y[GPW][SB];
+  Acc y[GPW][SB];
 #pragma unroll
   for (int gi = 0; gi < GPW; ++gi)
 #pragma unroll
@@ -509,7 +596,7 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
   }
   // X rows are read from the replicated lines, or straight from the staged copy when one row
   // already spans a whole bank line
-  constexpr bool kDup = NCOPY > 1;
+  constexpr bool kDup = NCOPY > 1 || DF;
   int64_t prevJ = -1;
   for (int64_t k = c0; k < c1; ++k) {
     const int s = (int)((k - c0) & 1);
@@ -532,12 +619,13 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
         const T* sxj = reinterpret_cast<const T*>(st + SL.xj);
         for (int e = tid; e < kMC * NB / EPL; e += NT) {
           const int c = (e * EPL) / NB, o = (e * EPL) % NB;
-          Vec<T, EPL> v;
-          if (c < avail) v = xj_bulk ? VecIO<T, EPL>::ld(sxj + c * NB + o) : VecIO<T, EPL>::ld(X + (cb0 + c) * NB + o);
-          else v.zero();
+          const T* src = xj_bulk ? sxj + c * NB + o : X + (cb0 + c) * NB + o;
 #pragma unroll
-          for (int p = 0; p < NCOPY; ++p)
-            VecIO<T, EPL>::st(reinterpret_cast<T*>(dup + (size_t)c * LINE + (size_t)p * RB) + o, v);
+          for (int p = 0; p < NCOPY; ++p) {
+            unsigned char* dst = dup + (size_t)c * LINE + (size_t)p * RB + (size_t)o * sizeof(T);
+            if (c < avail) Acc::stage(src, dst);
+            else Acc::stage_zero(dst);
+          }
         }
         __syncthreads();
       }
@@ -571,18 +659,14 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
         for (int qq = 0; qq < nq; ++qq) {
           const int base = (qo + qq) * 32 + i * 4;
           const uint32_t cq = *reinterpret_cast<const uint32_t*>(scol + base);
-          T vq[4];
-          QuadLoad<VS, T>::ld(sval + base, vq);
+          AT vq[4];
+          QuadLoad<VS, AT>::ld(sval + base, vq);
 #pragma unroll
           for (int jj = 0; jj < JJ; ++jj) {
             const int j = (M == 1) ? jj : sp + jj * M;
             const unsigned c = (cq >> (8 * j)) & 0xFFu;
-            const T v = (M == 1) ? vq[jj] : pick4(vq, j);
-            if (c != kPadCol) {
-              const Vec<T, EPL> x = VecIO<T, EPL>::ld(reinterpret_cast<const T*>(xbase + (size_t)c * LINE));
-#pragma unroll
-              for (int e = 0; e < EPL; ++e) y[gi][sb].v[e] = fma(v, x.v[e], y[gi][sb].v[e]);
-            }
+            const AT v = (M == 1) ? vq[jj] : pick4(vq, j);
+            if (c != kPadCol) y[gi][sb].add(v, Acc::load(xbase + (size_t)c * LINE));
           }
         }
       }
@@ -607,25 +691,20 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
   }
   // combine the step phases of each row (fixed xor tree), then one store per row slice
 #pragma unroll
-  for (int gi = 0; gi < GPW; ++gi)
+  for (int gi = 0; gi < GPW; ++gi) {
+    const int g = gi * WARPS + w;
 #pragma unroll
-    for (int sb = 0; sb < SB; ++sb)
+    for (int sb = 0; sb < SB; ++sb) {
+      Vec<T, EPL> out;
 #pragma unroll
       for (int e = 0; e < EPL; ++e) {
-        T v = y[gi][sb].v[e];
+        T v = y[gi][sb].get(e);
 #pragma unroll
         for (int o = RPI * L; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        y[gi][sb].v[e] = v;
+        out.v[e] = v;
       }
-  if (sp == 0) {
-#pragma unroll
-    for (int gi = 0; gi < GPW; ++gi) {
-      const int g = gi * WARPS + w;
-#pragma unroll
-      for (int sb = 0; sb < SB; ++sb) {
-        const int64_t r = r0 + g * kMG + rsub + sb * RPI;
-        if (r < a.n) VecIO<T, EPL>::st(Y + r * NB + q * EPL, y[gi][sb]);
-      }
+      const int64_t r = r0 + g * kMG + rsub + sb * RPI;
+      if (sp == 0 && r < a.n) VecIO<T, EPL>::st(Y + r * NB + q * EPL, out);
     }
   }
 }

@@ -17,11 +17,16 @@ def _plan(H, **kw):
 
 
 def _tol(H, X, Y_ref, dtype):
-    """Elementwise bound: k * eps * (|H| |X|)_i, k = 2 * max row length (sum + products)."""
+    """Elementwise bound: k * eps * (|H| |X|)_i, k = 2 * max row length (sum + products).
+    FP64 vectors with FP32/BF16 values are summed in double-float (two FP32 words): unit
+    roundoff 2^-44 per step instead of FP64's 2^-53."""
     absH = CSRUpper(H.n, H.rowptr, H.col, np.abs(H.values_f64()), "f64")
     bound = O.sym_upper_matmul(absH, np.abs(X))
     rowlen = np.diff(H.rowptr).max() * 2 + 2
-    eps = 2.0 ** -24 if dtype == torch.float32 else 2.0 ** -53
+    if dtype == torch.float32:
+        eps = 2.0 ** -24
+    else:
+        eps = 2.0 ** -53 if H.storage == "f64" else 2.0 ** -44
     return rowlen * eps * bound + 1e-300
 
 
