@@ -57,6 +57,8 @@ def parse():
                     help="switch to RMM-DIIS once every wanted relative residual is below this")
     ap.add_argument("--switch-tau", type=float, default=0.0,
                     help="switch on the eigenvalue-change rule tau <= this (0: off)")
+    ap.add_argument("--s-max", type=int, default=20,
+                    help="largest DIIS window of RMM-DIIS (Alg. 4 input s)")
     ap.add_argument("--layout", default="auto", choices=["auto", "mirrored", "half", "csr"],
                     help="device layout of the SpMM plan")
     return ap.parse_args()
@@ -212,7 +214,7 @@ def run_reference(args, ws, rank):
     ref0 = O.hybrid(H0, pad_rows(Z00, n0), args.nev, tol=args.tol, U=U0, rmm_maxiter=300,
                     rmm_precond="jacobi" if args.rmm_precond else "none",
                     switch_res=args.switch_res if args.switch_res > 0 else None,
-                    switch_tau_tol=args.switch_tau if args.switch_tau > 0 else None)
+                    switch_tau_tol=args.switch_tau if args.switch_tau > 0 else None, s_max=args.s_max)
     it_f, it_r = ref0.extra["front"].iterations, (ref0.extra["rmm"].iterations if ref0.extra["rmm"] else 0)
     X = np.random.default_rng(2).standard_normal((H.n, args.nb))
     times = []
@@ -254,7 +256,7 @@ def workload_config(args, H):
                          f"tol {args.tol:g}"),
             "n": H.n, "nnz_half": H.nnz, "n_ev": args.nev, "block": args.nb, "values": args.storage,
             "vectors": args.vec, "layout": args.layout, "switch_res": args.switch_res,
-            "switch_tau": args.switch_tau, "l2": "inputs larger than L2 (matrix ~3.2 GB), no flush",
+            "switch_tau": args.switch_tau, "s_max": args.s_max, "l2": "inputs larger than L2 (matrix ~3.2 GB), no flush",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
@@ -275,7 +277,7 @@ def main():
     S = binding.Solver(H, args.nev, args.nb, layout=args.layout)
     pinfo = S.spmm_info()
     opts = dict(vec_type=args.vec, tol=args.tol, timing=1, maxiter=500, rmm_precond=args.rmm_precond,
-                switch_res=args.switch_res, switch_tau=args.switch_tau)
+                switch_res=args.switch_res, switch_tau=args.switch_tau, s_max=args.s_max)
     st_ = torch.cuda.current_stream()
     for _ in range(args.warmup):
         S.solve("hybrid", X0=X0d, **opts)
@@ -313,7 +315,7 @@ def main():
         t = time.perf_counter()
         S2 = binding.Solver(H, args.nev, args.nb, layout=args.layout)
         S2.solve("hybrid", X0=X0, vec_type=args.vec, tol=args.tol, maxiter=500, rmm_precond=args.rmm_precond,
-                 switch_res=args.switch_res, switch_tau=args.switch_tau)
+                 switch_res=args.switch_res, switch_tau=args.switch_tau, s_max=args.s_max)
         S2.ritz()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t) * 1e3)

@@ -61,4 +61,43 @@ eig_status rmm_store_gram(double* B, const double* sums, Window win_after, int s
 
 int rmm_grid(int64_t n, int mp);
 
+// ---- FP32-vector step (rmm_mixed.cu): iterates in double-float (float2 per element), residual
+// history and every small quantity in FP32, dots in double-float then FP64; see that file. ----
+int rmx_grid(int64_t n, int mp);
+// Alg. 4 start from FP64 (x, Hx): x/||x|| as double-float into xh[slot], r (FP32) into rh[slot],
+// theta; partials [cta][j][2] of ||r||^2 (twice: the first row of the Gram store).
+eig_status rmx_start(const double* x0, const double* hx0, const double* num, const double* xnorm2, int mp, int64_t n,
+                     int slot, void* xh, float* rh, double* thh, double* theta_out, double* part, int* nparts,
+                     cudaStream_t st);
+// x~ and r_raw = H x~ - theta_ref x~ from the window (coef: [mp][3 kRmmSMax] from rmx_coef);
+// when w is given, w = r_raw for active columns and 0 otherwise; partials [cta][j][3] of
+// <x~,x~>, <x~,r_raw>, <x~, y^(newest)>.
+eig_status rmx_combine(const void* xh, const float* rh, const float* coef, Window win, int newest, const int* active,
+                       int mp, int64_t n, void* xt, float* rraw, float* w, double* part, int* nparts,
+                       cudaStream_t st);
+// The combine coefficients from the DIIS alpha, the Ritz values and the storage signs sg
+// ([kRmmSMax][mp], +-1) of the window.
+eig_status rmx_coef(const double* alpha, const double* thh, const double* sg, Window win, int newest, int mp,
+                    float* coef, cudaStream_t st);
+// Residual Gram row of the new slot with the storage signs applied.
+eig_status rmx_store_gram(double* B, const double* sums, const double* sg, Window win_after, int slot_new, int mp,
+                          cudaStream_t st);
+// w = K^{-1}(H x~ - theta~ x~) (Jacobi, floored) from the combine sums [mp][3].
+eig_status rmx_precond(const void* xt, const float* rraw, const double* sums, const double* theta_ref,
+                       const int* active, const double* diagH, double floor_, int mp, int64_t n, float* w,
+                       cudaStream_t st);
+// partials [cta][j][5]: <x~,w>, <w,w>, <w,r_raw>, <x~,Hw - theta_ref w>, <w,Hw - theta_ref w>.
+eig_status rmx_dots(const void* xt, const float* w, const float* rraw, const float* hw, const double* theta_ref,
+                    int mp, int64_t n, double* part, int* nparts, cudaStream_t st);
+// Shifted 2x2 Rayleigh-Ritz; theta and par[mp][5] = (g1, g2, mu, theta, storage sign).
+eig_status rmx_rr2(const double* s1, const double* s2, const double* theta_ref, const int* active, int mp,
+                   double* theta, double* par, cudaStream_t st);
+// New iterate and residual (times the storage sign) into slot_new; partials [cta][j][1 + win.s] of
+// ||r||^2 and <ry_new, ry^(i)>.
+eig_status rmx_update(const void* xt, const float* w, const float* rraw, const float* hw, const double* par,
+                      int slot_new, Window win_after, int mp, int64_t n, void* xh, float* rh, double* thh, double* sg,
+                      double* part, int* nparts, cudaStream_t st);
+// X (FP64, n x nev) = sign * (hi + lo) of the double-float iterate slot (n x mp).
+eig_status rmx_export(const void* xh_slot, const double* sgn, int mp, int nev, int64_t n, double* X, cudaStream_t st);
+
 }  // namespace eig

@@ -189,10 +189,16 @@ struct Carve {
   Carve(void* p, size_t c) : base((unsigned char*)p), cap(c) {}
   template <typename T> T* take(size_t count) {
     size_t b = (count * sizeof(T) + 255) & ~size_t(255);
+    if (off + b > cap) {  // sizing error: callers check ok() before any launch
+      bad = true;
+      return nullptr;
+    }
     T* r = (T*)(base + off);
     off += b;
     return r;
   }
+  bool ok() const { return !bad; }
+  bool bad = false;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -269,6 +275,7 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   void* rrwork = cv.take<unsigned char>(small_rr_work_bytes(kmax, nb));
   void* gpart = cv.take<unsigned char>(gram_scratch_bytes(12, nb));
   double* upart = cv.take<double>((size_t)ugrid * nb);
+  if (!cv.ok()) return EIG_EUNSUPPORTED;
   double* theta = stat;
   double* rsq = stat + nb;
   EIG_TRY(h->host.reserve((2 * nb + 8) * 8));
@@ -410,10 +417,157 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
 }
 
 // ---------------------------------------------------------------------------------------
+// batched RMM-DIIS (Alg. 4), FP32 vectors: double-float iterates, small quantities in FP32
+// (rmm_mixed.cu); same window, DIIS solve and 2x2 Rayleigh-Ritz as the FP64 step below
+// ---------------------------------------------------------------------------------------
+static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* iters, bool* converged,
+                                    std::vector<double>* theta_out) {
+  Handle* h = c.h;
+  const int nev = h->n_ev, mp = next_pow2(nev);
+  const int64_t n = h->n;
+  const int smax = std::max(1, std::min(c.o.s_max, kRmmSMax));
+  if (mp > 32) return EIG_EUNSUPPORTED;
+  if (h->plan.val_type == EIG_BF16) return EIG_EUNSUPPORTED;
+  const size_t slab = (size_t)n * mp;
+  // big: x history (double-float), r history (FP32), x~ (double-float), r_raw, w, Hw (FP32),
+  // and the FP64 start block and its product
+  const size_t big_bytes = smax * slab * 8 + smax * slab * 4 + slab * 8 + 3 * slab * 4 + 2 * slab * 8 + 8 * 256;
+  EIG_TRY(h->big.reserve(big_bytes));
+  Carve bc(h->big.p, h->big.bytes);
+  float2* xh = bc.take<float2>(smax * slab);
+  float* rh = bc.take<float>(smax * slab);
+  float2* xt = bc.take<float2>(slab);
+  float* rraw = bc.take<float>(slab);
+  float* w = bc.take<float>(slab);
+  float* hw = bc.take<float>(slab);
+  double* xs = bc.take<double>(slab);
+  double* hxs = bc.take<double>(slab);
+  const int grid = std::max(rmx_grid(n, mp), rmm_grid(n, mp));
+  const size_t small_bytes = (size_t)mp * kRmmSMax * kRmmSMax * 8 + mp * kRmmSMax * 8 + mp * 3 * kRmmSMax * 4 +
+                             mp * 5 * 8 + mp * 8 * 2 + mp * 4 + 2 * kRmmSMax * mp * 8 + mp * 8 +
+                             (size_t)grid * mp * (1 + kRmmSMax) * 8 + mp * (1 + kRmmSMax) * 8 * 3 +
+                             colsum_scratch_bytes(mp) + 16 * 256;
+  EIG_TRY(h->small.reserve(small_bytes));
+  Carve cv(h->small.p, h->small.bytes);
+  double* B = cv.take<double>((size_t)mp * kRmmSMax * kRmmSMax);
+  double* alpha = cv.take<double>((size_t)mp * kRmmSMax);
+  float* coef = cv.take<float>((size_t)mp * 3 * kRmmSMax);
+  double* par = cv.take<double>(mp * 5);
+  double* sg = cv.take<double>((size_t)kRmmSMax * mp);
+  double* theta = cv.take<double>(mp);
+  double* xn2 = cv.take<double>(mp);
+  int* active = cv.take<int>(mp);
+  double* thh = cv.take<double>(kRmmSMax * mp);
+  double* part = cv.take<double>((size_t)grid * mp * (1 + kRmmSMax));
+  double* sums = cv.take<double>((size_t)mp * (1 + kRmmSMax));
+  double* s1 = cv.take<double>((size_t)mp * (1 + kRmmSMax));
+  double* s2 = cv.take<double>((size_t)mp * (1 + kRmmSMax));
+  void* cpart = cv.take<unsigned char>(colsum_scratch_bytes(mp));
+  if (!bc.ok() || !cv.ok()) return EIG_EUNSUPPORTED;
+  EIG_TRY(h->host.reserve(mp * 2 * 8 + 64));
+  double* hstat = h->host.as<double>();
+  EIG_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)mp * kRmmSMax * kRmmSMax * 8, c.st));
+  // x^(0): accurate H x^(0) (double-float SpMM), theta^(0), r^(0) (Alg. 4 lines 2-4)
+  EIG_TRY(pad_columns(X0, nev, xs, mp, n, c.st));
+  EIG_TRY(col_sumsq(xs, mp, n, EIG_F64, xn2, cpart, c.st));
+  EIG_TRY(c.spmm(xs, hxs, mp, EIG_F64, nev));
+  {
+    const int threads = (256 / mp) * mp;
+    const int g2 = rmm_grid(n, mp);
+    k_coldot2<<<g2, threads, 0, c.st>>>(xs, hxs, nullptr, mp, n, part);
+    EIG_LAUNCH_CHECK("k_coldot2");
+    EIG_TRY(reduce_partials(part, g2, mp * 2, sums, c.st));
+    std::vector<double> hs(mp * 2);
+    EIG_CUDA_TRY(cudaMemcpyAsync(hs.data(), sums, mp * 2 * 8, cudaMemcpyDeviceToHost, c.st));
+    EIG_TRY(c.sync());
+    std::vector<double> num(mp);
+    for (int j = 0; j < mp; ++j) num[j] = hs[j * 2];
+    EIG_CUDA_TRY(cudaMemcpyAsync(s1, num.data(), mp * 8, cudaMemcpyHostToDevice, c.st));
+    int np = 0;
+    {
+      std::vector<double> ones((size_t)kRmmSMax * mp, 1.0);
+      EIG_CUDA_TRY(cudaMemcpyAsync(sg, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, c.st));
+    }
+    EIG_TRY(rmx_start(xs, hxs, s1, xn2, mp, n, 0, xh, rh, thh, theta, part, &np, c.st));
+    EIG_TRY(reduce_partials(part, np, mp * 2, sums, c.st));
+    Window w0;
+    w0.s = 1;
+    w0.slot[0] = 0;
+    EIG_TRY(rmm_store_gram(B, sums, w0, 0, mp, c.st));
+    std::vector<double> hs2(mp * 2);
+    EIG_CUDA_TRY(cudaMemcpyAsync(hs2.data(), sums, mp * 2 * 8, cudaMemcpyDeviceToHost, c.st));
+    EIG_CUDA_TRY(cudaMemcpyAsync(hstat, theta, mp * 8, cudaMemcpyDeviceToHost, c.st));
+    EIG_TRY(c.sync());
+    for (int j = 0; j < mp; ++j) hstat[mp + j] = hs2[j * 2];
+  }
+  std::vector<double> th(mp), rel(mp);
+  std::vector<int> act(mp, 0);
+  auto refresh = [&]() {
+    bool all = true;
+    for (int j = 0; j < mp; ++j) {
+      th[j] = hstat[j];
+      rel[j] = std::sqrt(std::max(hstat[mp + j], 0.0)) / std::max(std::fabs(th[j]), 1e-300);
+      act[j] = (j < nev && !(rel[j] < c.o.tol)) ? 1 : 0;
+      if (act[j]) all = false;
+    }
+    return all;
+  };
+  bool done = refresh();
+  c.trace(1, 0, th.data(), rel.data(), nev);
+  int count = 1, newest = 0, it = 0;
+  while (!done && it < maxiter) {
+    ++it;
+    EIG_CUDA_TRY(cudaMemcpyAsync(active, act.data(), mp * 4, cudaMemcpyHostToDevice, c.st));
+    Window win;
+    win.s = std::min(count, smax);
+    for (int i = 0; i < win.s; ++i) win.slot[i] = ((newest - (win.s - 1 - i)) % smax + smax) % smax;
+    EIG_TRY(rmm_diis(B, win, active, mp, alpha, c.st));
+    EIG_TRY(rmx_coef(alpha, thh, sg, win, newest, mp, coef, c.st));
+    const double* tref = thh + (size_t)newest * mp;
+    int np = 0;
+    EIG_TRY(rmx_combine(xh, rh, coef, win, newest, active, mp, n, xt, rraw, c.o.rmm_precond ? nullptr : w, part, &np,
+                        c.st));
+    EIG_TRY(reduce_partials(part, np, mp * 3, s1, c.st));
+    if (c.o.rmm_precond)
+      EIG_TRY(rmx_precond(xt, rraw, s1, tref, active, h->plan.diag.as<double>(), c.o.precond_floor, mp, n, w, c.st));
+    int nact = 0;
+    for (int j = 0; j < mp; ++j) nact += act[j];
+    EIG_TRY(c.spmm(w, hw, mp, EIG_F32, nact));
+    EIG_TRY(rmx_dots(xt, w, rraw, hw, tref, mp, n, part, &np, c.st));
+    EIG_TRY(reduce_partials(part, np, mp * 5, s2, c.st));
+    EIG_TRY(rmx_rr2(s1, s2, tref, active, mp, theta, par, c.st));
+    const int slot_new = (count < smax) ? count : (newest + 1) % smax;
+    Window wa;
+    wa.s = std::min(count + 1, smax);
+    for (int i = 0; i < wa.s; ++i) wa.slot[i] = ((slot_new - (wa.s - 1 - i)) % smax + smax) % smax;
+    EIG_TRY(rmx_update(xt, w, rraw, hw, par, slot_new, wa, mp, n, xh, rh, thh, sg, part, &np, c.st));
+    EIG_TRY(reduce_partials(part, np, mp * (1 + wa.s), sums, c.st));
+    EIG_TRY(rmx_store_gram(B, sums, sg, wa, slot_new, mp, c.st));
+    std::vector<double> hs((size_t)mp * (1 + wa.s));
+    EIG_CUDA_TRY(cudaMemcpyAsync(hs.data(), sums, hs.size() * 8, cudaMemcpyDeviceToHost, c.st));
+    EIG_CUDA_TRY(cudaMemcpyAsync(hstat, theta, mp * 8, cudaMemcpyDeviceToHost, c.st));
+    EIG_TRY(c.sync());
+    for (int j = 0; j < mp; ++j) hstat[mp + j] = hs[(size_t)j * (1 + wa.s)];
+    ++count;
+    newest = slot_new;
+    done = refresh();
+    c.trace(1, it, th.data(), rel.data(), nev);
+  }
+  *iters = it;
+  *converged = done;
+  theta_out->assign(th.begin(), th.begin() + nev);
+  EIG_TRY(h->Xres.reserve((size_t)n * nev * 8));
+  EIG_TRY(rmx_export(xh + (size_t)newest * slab, sg + (size_t)newest * mp, mp, nev, n, h->Xres.as<double>(), c.st));
+  EIG_TRY(c.sync());
+  return EIG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // batched RMM-DIIS (Alg. 4)
 // ---------------------------------------------------------------------------------------
 eig_status run_rmmdiis(Ctx& c, const double* X0, int maxiter, int* iters, bool* converged,
                        std::vector<double>* theta_out) {
+  if (c.o.vec_type == EIG_F32) return run_rmmdiis_mixed(c, X0, maxiter, iters, converged, theta_out);
   Handle* h = c.h;
   const int nev = h->n_ev, mp = next_pow2(nev);
   const int64_t n = h->n;
@@ -452,6 +606,7 @@ eig_status run_rmmdiis(Ctx& c, const double* X0, int maxiter, int* iters, bool* 
   double* sums2 = cv.take<double>((size_t)mp * (1 + kRmmSMax));
   double* xn2 = cv.take<double>(mp);
   void* cpart = cv.take<unsigned char>(colsum_scratch_bytes(mp));
+  if (!bc.ok() || !cv.ok()) return EIG_EUNSUPPORTED;
   EIG_TRY(h->host.reserve(mp * 2 * 8 + 64));
   double* hstat = h->host.as<double>();
   EIG_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)mp * kRmmSMax * kRmmSMax * 8, c.st));

@@ -191,3 +191,20 @@ def test_rmmdiis_preconditioned_matches_oracle_step_count():
     assert st["iterations_rmm"] <= 1.5 * ref.iterations + 5
     th, X, rel = S.ritz()
     np.testing.assert_allclose(th, lam, rtol=1e-10)
+
+
+@pytest.mark.parametrize("precond", [1])
+def test_rmmdiis_fp32_vectors_match_oracle(precond):
+    """The FP32-vector RMM-DIIS step (double-float iterates, shifted 2x2 pencil in FP32) follows
+    the FP64 oracle's Alg. 4 from the same start: same eigenpairs, at most a few more iterations.
+    (Without preconditioning the method needs hundreds of iterations here, in the oracle too.)"""
+    H = ci_matrix(3000, 100, 64, seed=3, storage="f32")
+    lam, Z = O.lowest_eigpairs(O.to_dense(H), 5)
+    X0 = Z + 1e-4 * random_block(H.n, 5, 5)
+    ref = O.rmmdiis(H, X0, tol=1e-6, maxiter=300, s_max=10, precond="jacobi" if precond else "none")
+    assert ref.converged
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("rmmdiis", X0=X0, vec_type="f32", s_max=10, rmm_precond=precond, tol=1e-6, maxiter=300)
+    assert rc == 0, st
+    assert st["iterations_rmm"] <= 1.5 * ref.iterations + 5, (st["iterations_rmm"], ref.iterations)
+    check_result(H, S, lam[:5])
