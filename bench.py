@@ -57,7 +57,7 @@ def parse():
                     help="switch to RMM-DIIS once every wanted relative residual is below this")
     ap.add_argument("--switch-tau", type=float, default=0.0,
                     help="switch on the eigenvalue-change rule tau <= this (0: off)")
-    ap.add_argument("--s-max", type=int, default=20,
+    ap.add_argument("--s-max", type=int, default=10,
                     help="largest DIIS window of RMM-DIIS (Alg. 4 input s)")
     ap.add_argument("--layout", default="auto", choices=["auto", "mirrored", "half", "csr"],
                     help="device layout of the SpMM plan")

@@ -290,87 +290,117 @@ __device__ __forceinline__ double jacobi_den(double d, double th, double floor) 
   return den < 0.0 ? -mag : mag;
 }
 
-template <typename T>
-__global__ void k_lobpcg_update(T* __restrict__ X, T* __restrict__ W, T* __restrict__ P, T* __restrict__ HX,
-                                const T* __restrict__ HW, T* __restrict__ HP, const double* __restrict__ C, int k,
-                                int nb, const double* __restrict__ theta, const double* __restrict__ diagH,
-                                double floor, int precond, int64_t n, double* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sC = reinterpret_cast<T*>(sm_raw);       // k x nb
-  double* sTh = reinterpret_cast<double*>(sC + ((k * nb + 1) & ~1));
-  double* red = sTh + nb;                      // blockDim
-  for (int i = threadIdx.x; i < k * nb; i += blockDim.x) sC[i] = (T)C[i];
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) sTh[i] = theta[i];
+// Jacobi denominator H_ii - theta, magnitude floored; FP32 is enough for a preconditioner.
+__device__ __forceinline__ float jacobi_den_f(double d, double th, float floor) {
+  const float den = (float)d - (float)th;
+  const float mag = fmaxf(fabsf(den), floor);
+  return den < 0.0f ? -mag : mag;
+}
+
+// Thread per (row, CPT adjacent columns); rows are read with 16-byte moves, the Rayleigh-Ritz
+// coefficients come from shared memory as CPT-wide vectors.  In place: the lanes of a row (one
+// warp) have read all their inputs before any of them writes (__syncwarp).
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+k_lobpcg_update(T* __restrict__ X, T* __restrict__ W, T* __restrict__ P, T* __restrict__ HX,
+                const T* __restrict__ HW, T* __restrict__ HP, const double* __restrict__ C, int k,
+                const double* __restrict__ theta, const double* __restrict__ diagH, double floor, int precond,
+                int64_t n, double* __restrict__ part) {
+  constexpr int CPT = (NB * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : NB;
+  constexpr int LPR = NB / CPT;           // lanes per row
+  constexpr int RPP = 256 / LPR;          // rows per pass
+  __shared__ __align__(16) T sC[3 * NB * NB];
+  __shared__ double red[256 * CPT];
+  for (int i = threadIdx.x; i < k * NB; i += blockDim.x) sC[i] = (T)C[i];
   __syncthreads();
-  const int rpp = blockDim.x / nb;            // rows per pass
-  const int j = threadIdx.x % nb, rr = threadIdx.x / nb;
-  const bool act = rr < rpp;
-  const double th = sTh[j];
-  double rsq = 0.0;
-  // the loop bound is uniform across the CTA so that __syncwarp sees every lane
-  for (int64_t base = blockIdx.x * (int64_t)rpp; base < n; base += (int64_t)gridDim.x * rpp) {
-    const int64_t r = base + rr;
-    const bool valid = act && r < n;
-    T xn = T(0), hxn = T(0), pn = T(0), hpn = T(0), wn = T(0);
-    if (valid) {
-      const T* xr = X + r * nb;
-      const T* hxr = HX + r * nb;
-      if (k == nb) {
-        xn = xr[j];
-        hxn = hxr[j];
-      } else {
-        T x = T(0), hx = T(0);
-        for (int l = 0; l < nb; ++l) {
-          const T c1 = sC[l * nb + j];
-          x = fma(xr[l], c1, x);
-          hx = fma(hxr[l], c1, hx);
+  const int j0 = (threadIdx.x % LPR) * CPT, rr = threadIdx.x / LPR;
+  double th[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) th[c] = theta[j0 + c];
+  double rsq[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) rsq[c] = 0.0;
+  float rh[CPT], rl[CPT];  // FP32 rows: double-float sums of squares
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) rh[c] = rl[c] = 0.0f;
+  // acc += A_row * Cblk[:, j0..j0+CPT) and hacc += HA_row * Cblk
+  auto gemv2 = [&](const T* A, const T* HA, int cb, Vec<T, CPT>& acc, Vec<T, CPT>& hacc) {
+#pragma unroll
+    for (int l0 = 0; l0 < NB; l0 += CPT) {
+      const Vec<T, CPT> a = VecIO<T, CPT>::ld(A + l0);
+      const Vec<T, CPT> ha = VecIO<T, CPT>::ld(HA + l0);
+#pragma unroll
+      for (int v = 0; v < CPT; ++v) {
+        const Vec<T, CPT> cv = VecIO<T, CPT>::ld(sC + (cb + l0 + v) * NB + j0);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          acc.v[c] = fma(a.v[v], cv.v[c], acc.v[c]);
+          hacc.v[c] = fma(ha.v[v], cv.v[c], hacc.v[c]);
         }
-        const T* wr = W + r * nb;
-        const T* hwr = HW + r * nb;
-        for (int l = 0; l < nb; ++l) {
-          const T c2 = sC[(nb + l) * nb + j];
-          pn = fma(wr[l], c2, pn);
-          hpn = fma(hwr[l], c2, hpn);
-        }
-        if (k == 3 * nb) {
-          const T* pr = P + r * nb;
-          const T* hpr = HP + r * nb;
-          for (int l = 0; l < nb; ++l) {
-            const T c3 = sC[(2 * nb + l) * nb + j];
-            pn = fma(pr[l], c3, pn);
-            hpn = fma(hpr[l], c3, hpn);
-          }
-        }
-        xn = x + pn;
-        hxn = hx + hpn;
       }
-      const T res = hxn - (T)th * xn;
-      rsq += (double)res * (double)res;
-      wn = res;
-      if (precond == 1) wn = (T)((double)res / jacobi_den(diagH[r], th, floor));
     }
-    __syncwarp();  // the nb lanes of a row (one warp) have read their inputs before any write
+  };
+  // the loop bound is uniform across the CTA so that __syncwarp sees every lane
+  for (int64_t base = blockIdx.x * (int64_t)RPP; base < n; base += (int64_t)gridDim.x * RPP) {
+    const int64_t r = base + rr;
+    const bool valid = r < n;
+    Vec<T, CPT> xn, hxn, pn, hpn, wn;
+    xn.zero(); hxn.zero(); pn.zero(); hpn.zero(); wn.zero();
     if (valid) {
-      if (k != nb) {
-        X[r * nb + j] = xn;
-        HX[r * nb + j] = hxn;
-        P[r * nb + j] = pn;
-        HP[r * nb + j] = hpn;
+      if (k == NB) {
+        xn = VecIO<T, CPT>::ld(X + r * NB + j0);
+        hxn = VecIO<T, CPT>::ld(HX + r * NB + j0);
+      } else {
+        gemv2(X + r * NB, HX + r * NB, 0, xn, hxn);
+        gemv2(W + r * NB, HW + r * NB, NB, pn, hpn);
+        if (k == 3 * NB) gemv2(P + r * NB, HP + r * NB, 2 * NB, pn, hpn);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          xn.v[c] += pn.v[c];
+          hxn.v[c] += hpn.v[c];
+        }
       }
-      W[r * nb + j] = wn;
+      const double d = diagH[r];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const T res = hxn.v[c] - (T)th[c] * xn.v[c];
+        if (sizeof(T) == 4) {
+          // exact FP32 square summed in double-float
+          const float f = (float)res, p = f * f, pe = fmaf(f, f, -p);
+          const float s = rh[c] + p, bb = s - rh[c];
+          rl[c] += ((rh[c] - (s - bb)) + (p - bb)) + pe;
+          rh[c] = s;
+          wn.v[c] = precond == 1 ? (T)(f / jacobi_den_f(d, th[c], (float)floor)) : res;
+        } else {
+          rsq[c] = fma((double)res, (double)res, rsq[c]);
+          wn.v[c] = precond == 1 ? (T)((double)res / jacobi_den(d, th[c], floor)) : res;
+        }
+      }
+    }
+    __syncwarp();
+    if (valid) {
+      if (k != NB) {
+        VecIO<T, CPT>::st(X + r * NB + j0, xn);
+        VecIO<T, CPT>::st(HX + r * NB + j0, hxn);
+        VecIO<T, CPT>::st(P + r * NB + j0, pn);
+        VecIO<T, CPT>::st(HP + r * NB + j0, hpn);
+      }
+      VecIO<T, CPT>::st(W + r * NB + j0, wn);
     }
   }
-  red[threadIdx.x] = act ? rsq : 0.0;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) red[threadIdx.x * CPT + c] = rsq[c] + (double)rh[c] + (double)rl[c];
   __syncthreads();
-  if (threadIdx.x < nb) {
+  for (int j = threadIdx.x; j < NB; j += blockDim.x) {
+    const int g = j / CPT, c = j % CPT;
     double t = 0.0;
-    for (int q = 0; q < rpp; ++q) t += red[q * nb + threadIdx.x];
-    part[(size_t)blockIdx.x * nb + threadIdx.x] = t;
+    for (int q = 0; q < RPP; ++q) t += red[(q * LPR + g) * CPT + c];
+    part[(size_t)blockIdx.x * NB + j] = t;
   }
 }
 
 int update_grid(int64_t n) {
-  int64_t g = (n + 15) / 16;
+  int64_t g = (n + 63) / 64;
   const int64_t cap = (int64_t)num_sms() * 8;
   return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
 }
@@ -381,18 +411,27 @@ eig_status lobpcg_update(void* X, void* W, void* P, void* HX, void* HW, void* HP
   if (nb < 1 || nb > 32 || 32 % nb != 0 || (k != nb && k != 2 * nb && k != 3 * nb)) return EIG_EINVAL;
   const int grid = update_grid(n);
   if (grid > nparts_max) return EIG_EINVAL;
-  const int threads = 256;
-  const size_t sm = (size_t)((k * nb + 1) & ~1) * (vt == EIG_F64 ? 8 : 4) + (size_t)nb * 8 + threads * 8;
+#define EIG_UPD(T, NBV)                                                                                    \
+  k_lobpcg_update<T, NBV><<<grid, 256, 0, st>>>((T*)X, (T*)W, (T*)P, (T*)HX, (const T*)HW, (T*)HP, C, k, theta, \
+                                                diagH, floor, precond, n, part)
+#define EIG_UPD_NB(T)                  \
+  switch (nb) {                        \
+    case 1: EIG_UPD(T, 1); break;      \
+    case 2: EIG_UPD(T, 2); break;      \
+    case 4: EIG_UPD(T, 4); break;      \
+    case 8: EIG_UPD(T, 8); break;      \
+    case 16: EIG_UPD(T, 16); break;    \
+    default: EIG_UPD(T, 32); break;    \
+  }
   if (vt == EIG_F32) {
-    k_lobpcg_update<float><<<grid, threads, sm, st>>>((float*)X, (float*)W, (float*)P, (float*)HX, (const float*)HW,
-                                                      (float*)HP, C, k, nb, theta, diagH, floor, precond, n, part);
+    EIG_UPD_NB(float)
   } else if (vt == EIG_F64) {
-    k_lobpcg_update<double><<<grid, threads, sm, st>>>((double*)X, (double*)W, (double*)P, (double*)HX,
-                                                       (const double*)HW, (double*)HP, C, k, nb, theta, diagH, floor,
-                                                       precond, n, part);
+    EIG_UPD_NB(double)
   } else {
     return EIG_EINVAL;
   }
+#undef EIG_UPD_NB
+#undef EIG_UPD
   EIG_LAUNCH_CHECK("k_lobpcg_update");
   *nparts_out = grid;
   return EIG_OK;

@@ -232,67 +232,92 @@ k_rmm_start(double* __restrict__ x, const double* __restrict__ hx, const double*
   cta_colreduce<2>(v, mp, red, part);
 }
 
-__global__ void k_rmm_diis(const double* __restrict__ B, Window win, const int* __restrict__ active, int mp,
-                           double* __restrict__ alpha) {
-  const int j = threadIdx.x;
+// One warp per column j (CTA j): lane i owns row i of the (s-1)x(s-1) system, kept in shared
+// memory; each entry is computed with the same operations in the same order as a sequential
+// Cholesky would, so the result does not depend on the parallel layout.
+__global__ void __launch_bounds__(32) k_rmm_diis(const double* __restrict__ B, Window win,
+                                                 const int* __restrict__ active, int mp, double* __restrict__ alpha) {
+  constexpr int M = kRmmSMax - 1;
+  __shared__ double F[M][M + 1];
+  __shared__ double rhs[M], y[M];
+  __shared__ int fail;
+  const int j = blockIdx.x, lane = threadIdx.x;
   if (j >= mp) return;
   double* al = alpha + j * kRmmSMax;
-  for (int i = 0; i < kRmmSMax; ++i) al[i] = 0.0;
+  for (int i = lane; i < kRmmSMax; i += 32) al[i] = 0.0;
+  __syncwarp();
   const int s = win.s;
   if (!active[j] || s <= 1) {
-    al[s - 1] = 1.0;
+    if (lane == 0) al[s - 1] = 1.0;
     return;
   }
   const double* Bj = B + (size_t)j * kRmmSMax * kRmmSMax;
   const int l = win.slot[s - 1];
   const double bll = Bj[l * kRmmSMax + l];
-  double F[kRmmSMax - 1][kRmmSMax - 1];
-  double rhs[kRmmSMax - 1], y[kRmmSMax - 1];
   for (int first = 0; first < s - 1; ++first) {
     const int m = s - 1 - first;  // unknowns: window entries first .. s-2
-    double mx = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const int si = win.slot[first + i];
-      rhs[i] = -(Bj[si * kRmmSMax + l] - bll);
+    double fii = 0.0;
+    if (lane < m) {
+      const int si = win.slot[first + lane];
+      rhs[lane] = -(Bj[si * kRmmSMax + l] - bll);
       for (int k = 0; k < m; ++k) {
         const int sk = win.slot[first + k];
-        F[i][k] = Bj[si * kRmmSMax + sk] - Bj[si * kRmmSMax + l] - Bj[l * kRmmSMax + sk] + bll;
+        F[lane][k] = Bj[si * kRmmSMax + sk] - Bj[si * kRmmSMax + l] - Bj[l * kRmmSMax + sk] + bll;
       }
-      mx = fmax(mx, F[i][i]);
+      fii = F[lane][lane];
     }
-    bool ok = mx > 0.0;
-    for (int c = 0; c < m && ok; ++c) {
-      double piv = F[c][c];
-      for (int q = 0; q < c; ++q) piv -= F[c][q] * F[c][q];
-      if (!(piv > 1e-13 * mx)) { ok = false; break; }
-      const double lcc = sqrt(piv);
-      F[c][c] = lcc;
-      for (int i = c + 1; i < m; ++i) {
-        double t = F[i][c];
-        for (int q = 0; q < c; ++q) t -= F[i][q] * F[c][q];
-        F[i][c] = t / lcc;
+    // max of the diagonal, in the sequential order
+    if (lane == 0) fail = 0;
+    __syncwarp();
+    double mx = 0.0;
+    if (lane == 0) {
+      for (int i = 0; i < m; ++i) mx = fmax(mx, F[i][i]);
+      if (!(mx > 0.0)) fail = 1;
+    }
+    (void)fii;
+    mx = __shfl_sync(0xffffffffu, mx, 0);
+    __syncwarp();
+    for (int c = 0; c < m && !fail; ++c) {
+      if (lane == c) {
+        double piv = F[c][c];
+        for (int q = 0; q < c; ++q) piv -= F[c][q] * F[c][q];
+        if (!(piv > 1e-13 * mx)) fail = 1;
+        else F[c][c] = sqrt(piv);
       }
+      __syncwarp();
+      if (fail) break;
+      if (lane > c && lane < m) {
+        double t = F[lane][c];
+        for (int q = 0; q < c; ++q) t -= F[lane][q] * F[c][q];
+        F[lane][c] = t / F[c][c];
+      }
+      __syncwarp();
     }
-    if (!ok) continue;  // drop the oldest entry and retry
-    for (int i = 0; i < m; ++i) {
-      double t = rhs[i];
-      for (int q = 0; q < i; ++q) t -= F[i][q] * y[q];
-      y[i] = t / F[i][i];
+    if (fail) {  // drop the oldest entry and retry
+      __syncwarp();
+      continue;
     }
-    for (int i = m - 1; i >= 0; --i) {
-      double t = y[i];
-      for (int q = i + 1; q < m; ++q) t -= F[q][i] * y[q];
-      y[i] = t / F[i][i];
+    if (lane == 0) {
+      for (int i = 0; i < m; ++i) {
+        double t = rhs[i];
+        for (int q = 0; q < i; ++q) t -= F[i][q] * y[q];
+        y[i] = t / F[i][i];
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double t = y[i];
+        for (int q = i + 1; q < m; ++q) t -= F[q][i] * y[q];
+        y[i] = t / F[i][i];
+      }
+      double sum = 0.0;
+      for (int i = 0; i < m; ++i) {
+        al[first + i] = y[i];
+        sum += y[i];
+      }
+      al[s - 1] = 1.0 - sum;
     }
-    double sum = 0.0;
-    for (int i = 0; i < m; ++i) {
-      al[first + i] = y[i];
-      sum += y[i];
-    }
-    al[s - 1] = 1.0 - sum;
     return;
   }
-  al[s - 1] = 1.0;  // every difference system singular: keep the newest iterate
+  if (lane == 0) al[s - 1] = 1.0;  // every difference system singular: keep the newest iterate
 }
 
 __global__ void k_rmm_store_gram(double* __restrict__ B, const double* __restrict__ sums, Window win, int slot_new,
@@ -379,7 +404,7 @@ eig_status rmm_start(double* x, const double* hx, const double* num, const doubl
 }
 
 eig_status rmm_diis(const double* B, Window win, const int* active, int mp, double* alpha, cudaStream_t st) {
-  k_rmm_diis<<<1, 32, 0, st>>>(B, win, active, mp, alpha);
+  k_rmm_diis<<<mp, 32, 0, st>>>(B, win, active, mp, alpha);
   EIG_LAUNCH_CHECK("k_rmm_diis");
   return EIG_OK;
 }

@@ -530,12 +530,15 @@ template <typename T, int NB> struct MirrorShape {
   static constexpr int LINE = RB < 128 ? 128 : RB;    // bytes of one replicated X row
   // registers of y per lane with 4 warps (32-bit words); more warps when it is large
   static constexpr int YREG4 = (kMGroups / 4) * SB * EPL * (int)sizeof(T) / 4;
-  static constexpr int WARPS = YREG4 > 48 ? 8 : 4;
+  // 4 warps for FP32 vectors (measured fastest); 8 for FP64-sized elements, whose
+  // double-float or FP64 arithmetic gains from more resident warps
+  static constexpr int WARPS = (sizeof(T) == 8 || YREG4 > 48) ? 8 : 4;
+  static constexpr int MINB = WARPS == 4 ? 2 : (YREG4 > 48 ? 2 : 3);   // resident CTAs aimed for
   static constexpr int GPW = kMGroups / WARPS;
 };
 
 template <typename T, typename V, int NB>
-__global__ void __launch_bounds__(MirrorShape<T, NB>::WARPS * 32, MirrorShape<T, NB>::WARPS == 8 ? 1 : 2)
+__global__ void __launch_bounds__(MirrorShape<T, NB>::WARPS * 32, MirrorShape<T, NB>::MINB)
 k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_bulk) {
   typedef MirrorShape<T, NB> Sh;
   constexpr int EPL = Sh::EPL, L = Sh::L, RPI = Sh::RPI, SB = Sh::SB, M = Sh::M, JJ = Sh::JJ;
