@@ -204,7 +204,10 @@ struct Carve {
 // ---------------------------------------------------------------------------------------
 // certification: true FP64 residuals of (theta_j, x_j) for the returned pairs
 // ---------------------------------------------------------------------------------------
-eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, std::vector<double>* relres) {
+// Also flags duplicates: two returned vectors that are collinear (|cos| >= 0.9) with Ritz values
+// equal to 1e-6 relative (RMM-DIIS does not orthogonalise its vectors, Sec. 3.3).
+eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, std::vector<double>* relres,
+                   bool* duplicate) {
   Handle* h = c.h;
   const int m = h->n_ev, mp = next_pow2(m);
   const int64_t n = h->n;
@@ -242,6 +245,28 @@ eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, st
   for (int j = 0; j < m; ++j) {
     const double xn = std::sqrt(std::max(nn[j], 1e-300));
     (*relres)[j] = std::sqrt(std::max(hs[j * 2 + 1], 0.0)) / xn / std::max(std::fabs(theta[j]), 1e-300);
+  }
+  // Gram of the returned vectors
+  *duplicate = false;
+  if (m > 1) {
+    DevBuf gbuf;
+    EIG_TRY(gbuf.reserve((size_t)mp * mp * 8 + gram_scratch_bytes(1, mp)));
+    double* G = gbuf.as<double>();
+    BlockList bl;
+    bl.n = 1;
+    bl.p[0] = Xp;
+    const int pa = 0, pb = 0;
+    EIG_TRY(gram_multi(bl, &pa, &pb, 1, mp, n, EIG_F64, G, G + (size_t)mp * mp, c.st));
+    std::vector<double> hg((size_t)mp * mp);
+    EIG_CUDA_TRY(cudaMemcpyAsync(hg.data(), G, hg.size() * 8, cudaMemcpyDeviceToHost, c.st));
+    EIG_TRY(c.sync());
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j) {
+        const double gi = hg[(size_t)i * mp + i], gj = hg[(size_t)j * mp + j];
+        const double cosv = std::fabs(hg[(size_t)i * mp + j]) / std::sqrt(std::max(gi * gj, 1e-300));
+        const double scale = std::max(std::max(std::fabs(theta[i]), std::fabs(theta[j])), 1e-300);
+        if (cosv >= 0.9 && std::fabs(theta[i] - theta[j]) <= 1e-6 * scale) *duplicate = true;
+      }
   }
   return EIG_OK;
 }
@@ -970,8 +995,9 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
   h->have = true;
   // true FP64 residuals of the returned pairs
   std::vector<double> rel;
+  bool dup = false;
   if (c.o.certify) {
-    EIG_TRY(certify(c, h->Xres.as<double>(), h->theta, &rel));
+    EIG_TRY(certify(c, h->Xres.as<double>(), h->theta, &rel, &dup));
   } else {
     rel.assign(nev, NAN);
   }
@@ -1002,6 +1028,7 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
     cudaEventDestroy(t1);
     cudaEventDestroy(t2);
   }
+  if (dup) return EIG_EDUPLICATE;
   return conv ? EIG_OK : EIG_ENOT_CONVERGED;
 }
 

@@ -208,3 +208,19 @@ def test_rmmdiis_fp32_vectors_match_oracle(precond):
     assert rc == 0, st
     assert st["iterations_rmm"] <= 1.5 * ref.iterations + 5, (st["iterations_rmm"], ref.iterations)
     check_result(H, S, lam[:5])
+
+
+def test_rmmdiis_duplicate_start_reported():
+    """RMM-DIIS keeps no orthogonality between its vectors (Sec. 3.3): two identical start vectors
+    stay on the same eigenpair.  The certification detects the collinear pair and the solve
+    returns EIG_EDUPLICATE (eig_ritz still returns the pairs)."""
+    from paper_2305_15552_gb300 import binding
+    H = ci_matrix(3000, 100, 64, seed=3, storage="f64")
+    lam, Z = O.lowest_eigpairs(O.to_dense(H), 5)
+    X0 = Z.copy()
+    X0[:, 1] = X0[:, 0]
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("rmmdiis", X0=X0, vec_type="f64", s_max=10, rmm_precond=1, tol=1e-8, maxiter=50)
+    assert rc == binding.EIG_EDUPLICATE, (rc, st)
+    th, X, rel = S.ritz()
+    assert abs(th[0] - th[1]) <= 1e-8 * abs(th[0])
