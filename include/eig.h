@@ -240,6 +240,10 @@ typedef struct {
   int trace_cap;           /* iteration [phase (0 front/single, 1 RMM-DIIS), iteration,             */
                            /* theta_1..theta_nev, relres_1..relres_nev] (the convergence histories  */
                            /* of Sec. 3.2); NULL = off                                              */
+  int rmm_maxiter;         /* hybrid: RMM-DIIS iteration limit (0 = maxiter)                        */
+  int rmm_fallback;        /* hybrid: when RMM-DIIS ends unconverged or with two collinear vectors, */
+                           /* finish with LOBPCG on FP64 vectors from its result (default 1; 0 =   */
+                           /* the paper's hybrid as printed, which has no remedy for that case)    */
 } eig_opts;
 
 typedef struct {
@@ -261,6 +265,7 @@ typedef struct {
                            /* of the stored triangle (values + int32 columns) and rowptr, X read   */
                            /* and Y written once                                                     */
   int trace_rows;          /* rows written to opts->trace                                           */
+  int iterations_fallback; /* LOBPCG iterations of the hybrid's fallback (0 when not needed)        */
 } eig_stats;
 
 /* Fills *o with the defaults documented in eig_opts. */

@@ -49,7 +49,7 @@ class Opts(C.Structure):
                 ("cheb_degree", C.c_int), ("lambda_ub", C.c_double), ("lanczos_maxbasis", C.c_int),
                 ("X0", C.c_void_p), ("x0_cols", C.c_int), ("x0_on_device", C.c_int), ("seed", C.c_uint64),
                 ("certify", C.c_int), ("timing", C.c_int), ("stream", C.c_void_p), ("trace", C.c_void_p),
-                ("trace_cap", C.c_int)]
+                ("trace_cap", C.c_int), ("rmm_maxiter", C.c_int), ("rmm_fallback", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -57,7 +57,8 @@ class Stats(C.Structure):
                 ("switch_reason", C.c_int), ("spmm_calls", C.c_int64), ("spmv_count", C.c_int64),
                 ("last_tau", C.c_double), ("max_relres", C.c_double), ("time_ms_total", C.c_double),
                 ("time_ms_spmm", C.c_double), ("time_ms_front", C.c_double), ("time_ms_rmm", C.c_double),
-                ("spmm_timed", C.c_int64), ("spmm_bytes", C.c_double), ("trace_rows", C.c_int)]
+                ("spmm_timed", C.c_int64), ("spmm_bytes", C.c_double), ("trace_rows", C.c_int),
+                ("iterations_fallback", C.c_int)]
 
 
 _SIGS = {

@@ -204,6 +204,33 @@ struct Carve {
 // ---------------------------------------------------------------------------------------
 // certification: true FP64 residuals of (theta_j, x_j) for the returned pairs
 // ---------------------------------------------------------------------------------------
+// Two columns of X (n x ld, FP64, first m used) that are collinear (|cos| >= 0.9) with Ritz values
+// equal to 1e-6 relative: RMM-DIIS does not orthogonalise its vectors (Sec. 3.3).
+eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::vector<double>& theta,
+                           bool* duplicate) {
+  *duplicate = false;
+  if (m < 2) return EIG_OK;
+  DevBuf gbuf;
+  EIG_TRY(gbuf.reserve((size_t)ld * ld * 8 + gram_scratch_bytes(1, ld)));
+  double* G = gbuf.as<double>();
+  BlockList bl;
+  bl.n = 1;
+  bl.p[0] = X;
+  const int pa = 0, pb = 0;
+  EIG_TRY(gram_multi(bl, &pa, &pb, 1, ld, c.h->n, EIG_F64, G, G + (size_t)ld * ld, c.st));
+  std::vector<double> hg((size_t)ld * ld);
+  EIG_CUDA_TRY(cudaMemcpyAsync(hg.data(), G, hg.size() * 8, cudaMemcpyDeviceToHost, c.st));
+  EIG_TRY(c.sync());
+  for (int i = 0; i < m; ++i)
+    for (int j = i + 1; j < m; ++j) {
+      const double gi = hg[(size_t)i * ld + i], gj = hg[(size_t)j * ld + j];
+      const double cosv = std::fabs(hg[(size_t)i * ld + j]) / std::sqrt(std::max(gi * gj, 1e-300));
+      const double scale = std::max(std::max(std::fabs(theta[i]), std::fabs(theta[j])), 1e-300);
+      if (cosv >= 0.9 && std::fabs(theta[i] - theta[j]) <= 1e-6 * scale) *duplicate = true;
+    }
+  return EIG_OK;
+}
+
 // Also flags duplicates: two returned vectors that are collinear (|cos| >= 0.9) with Ritz values
 // equal to 1e-6 relative (RMM-DIIS does not orthogonalise its vectors, Sec. 3.3).
 eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, std::vector<double>* relres,
@@ -246,28 +273,7 @@ eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, st
     const double xn = std::sqrt(std::max(nn[j], 1e-300));
     (*relres)[j] = std::sqrt(std::max(hs[j * 2 + 1], 0.0)) / xn / std::max(std::fabs(theta[j]), 1e-300);
   }
-  // Gram of the returned vectors
-  *duplicate = false;
-  if (m > 1) {
-    DevBuf gbuf;
-    EIG_TRY(gbuf.reserve((size_t)mp * mp * 8 + gram_scratch_bytes(1, mp)));
-    double* G = gbuf.as<double>();
-    BlockList bl;
-    bl.n = 1;
-    bl.p[0] = Xp;
-    const int pa = 0, pb = 0;
-    EIG_TRY(gram_multi(bl, &pa, &pb, 1, mp, n, EIG_F64, G, G + (size_t)mp * mp, c.st));
-    std::vector<double> hg((size_t)mp * mp);
-    EIG_CUDA_TRY(cudaMemcpyAsync(hg.data(), G, hg.size() * 8, cudaMemcpyDeviceToHost, c.st));
-    EIG_TRY(c.sync());
-    for (int i = 0; i < m; ++i)
-      for (int j = i + 1; j < m; ++j) {
-        const double gi = hg[(size_t)i * mp + i], gj = hg[(size_t)j * mp + j];
-        const double cosv = std::fabs(hg[(size_t)i * mp + j]) / std::sqrt(std::max(gi * gj, 1e-300));
-        const double scale = std::max(std::max(std::fabs(theta[i]), std::fabs(theta[j])), 1e-300);
-        if (cosv >= 0.9 && std::fabs(theta[i] - theta[j]) <= 1e-6 * scale) *duplicate = true;
-      }
-  }
+  EIG_TRY(find_duplicates(c, Xp, m, mp, theta, duplicate));
   return EIG_OK;
 }
 
@@ -783,6 +789,8 @@ void eig_default_opts(eig_opts* o) {
   o->seed = 1;
   o->certify = 1;
   o->timing = 0;
+  o->rmm_maxiter = 0;
+  o->rmm_fallback = 1;
   o->stream = nullptr;
 }
 
@@ -926,8 +934,40 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
     }
     Xf.release();
     int rit = 0;
-    EIG_TRY(run_rmmdiis(c, Xs.as<double>(), c.o.maxiter, &rit, &conv, &theta));
+    EIG_TRY(run_rmmdiis(c, Xs.as<double>(), c.o.rmm_maxiter > 0 ? c.o.rmm_maxiter : c.o.maxiter, &rit, &conv,
+                        &theta));
     c.s->iterations_rmm = rit;
+    bool dup = false;
+    if (c.o.rmm_fallback) EIG_TRY(find_duplicates(c, h->Xres.as<double>(), nev, nev, theta, &dup));
+    if (c.o.rmm_fallback && (!conv || dup)) {
+      // LOBPCG on FP64 vectors (a subspace method: it separates what RMM-DIIS let drift together)
+      // from the RMM-DIIS vectors, to the requested tolerance
+      const eig_dtype vt_saved = c.o.vec_type;
+      c.o.vec_type = EIG_F64;
+      int fit = 0, freason = 0;
+      bool fc = false;
+      DevBuf Xf2, X0f;
+      EIG_TRY(Xf2.reserve((size_t)n * nb * 8));
+      EIG_TRY(X0f.reserve((size_t)n * nev * 8));
+      EIG_CUDA_TRY(cudaMemcpyAsync(X0f.p, h->Xres.p, (size_t)n * nev * 8, cudaMemcpyDeviceToDevice, c.st));
+      const eig_status fr = run_lobpcg(c, X0f.as<double>(), nev, c.o.maxiter, StopFn(), &fit, &freason, &fc,
+                                       Xf2.as<double>(), &theta);
+      c.o.vec_type = vt_saved;
+      EIG_TRY(fr);
+      c.s->iterations_fallback = fit;
+      BlockList in;
+      in.n = 1;
+      in.p[0] = Xf2.p;
+      std::vector<double> M((size_t)nb * nev, 0.0);
+      for (int j = 0; j < nev; ++j) M[(size_t)j * nev + j] = 1.0;
+      DevBuf dM;
+      EIG_TRY(dM.reserve(M.size() * 8));
+      EIG_CUDA_TRY(cudaMemcpyAsync(dM.p, M.data(), M.size() * 8, cudaMemcpyHostToDevice, c.st));
+      EIG_TRY(block_apply(in, nb, dM.as<double>(), nev, h->Xres.p, 0.0, n, EIG_F64, c.st));
+      EIG_TRY(c.sync());
+      theta.resize(nev);
+      conv = fc;
+    }
     return EIG_OK;
   };
   switch (method) {

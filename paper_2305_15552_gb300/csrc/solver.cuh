@@ -89,6 +89,8 @@ eig_status fill_random(double* X, int64_t count, uint64_t seed, cudaStream_t st)
 eig_status pad_columns(const double* src, int ks, double* dst, int kd, int64_t n, cudaStream_t st);
 // dst (n x kd) columns j < min(ks, kd) <- src (n x ks); other columns untouched
 eig_status overlay_columns(const double* src, int ks, double* dst, int kd, int64_t n, cudaStream_t st);
+eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::vector<double>& theta,
+                           bool* duplicate);
 eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, std::vector<double>* relres,
                    bool* duplicate);
 inline int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }

@@ -224,3 +224,19 @@ def test_rmmdiis_duplicate_start_reported():
     assert rc == binding.EIG_EDUPLICATE, (rc, st)
     th, X, rel = S.ritz()
     assert abs(th[0] - th[1]) <= 1e-8 * abs(th[0])
+
+
+def test_hybrid_fallback_when_rmmdiis_stops_early(H3000f):
+    """A switch after one front iteration and a 3-iteration RMM-DIIS budget leave the pairs
+    unconverged: with the fallback (default) the hybrid finishes with FP64-vector LOBPCG and
+    meets the tolerance; without it, it reports EIG_ENOT_CONVERGED."""
+    from paper_2305_15552_gb300 import binding
+    H, lam = H3000f
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type="f32", switch_after=1, rmm_maxiter=3, rmm_precond=1)
+    assert rc == 0, st
+    assert st["iterations_rmm"] == 3 and st["iterations_fallback"] > 0, st
+    check_result(H, S, lam[:5])
+    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type="f32", switch_after=1, rmm_maxiter=3, rmm_precond=1,
+                     rmm_fallback=0)
+    assert rc == binding.EIG_ENOT_CONVERGED and st["iterations_fallback"] == 0, st
