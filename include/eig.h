@@ -145,9 +145,9 @@ EIG_API eig_status eig_spmm_plan_info(const void* plan, eig_spmm_info* info);
  * partial products is owned by the plan (grown on demand; the first call for a given
  * (nb, vec_type) may allocate).  Deterministic: results are bitwise reproducible.
  * Arithmetic: FP32 vectors in FP32; FP64 vectors with FP64 values in FP64; FP64 vectors with
- * FP32 values in the mirrored layout in double-float (exact FP32 products summed as two FP32
+ * FP32 or BF16 values in the mirrored layout in double-float (exact FP32 products summed as two FP32
  * words, ~2^-44 relative per step), which sm_103a runs at FP32 rate.
- * Supported (matrix, vector) types: (F32,F32), (F64,F64), (BF16,F32), (F32,F64). */
+ * Supported (matrix, vector) types: (F32,F32), (F64,F64), (BF16,F32), (F32,F64), (BF16,F64). */
 EIG_API eig_status eig_spmm(void* plan, const void* X, void* Y, int nb, eig_dtype vec_type, void* stream);
 
 /* Gram product G = A^T B (Eq. rreig's S^T S / S^T H S; Eq. bgs's V^T W).  A, B: device, row-major
@@ -225,7 +225,8 @@ typedef struct {
                            /* RMM-DIIS iterates) or EIG_F64 (every vector in FP64)                  */
   int precond;             /* LOBPCG K^{-1} of Eq. (wblock): 0 none, 1 Jacobi (default)              */
   int rmm_precond;         /* RMM-DIIS: 0 W = (x~, r~) as Alg. 4 (default), 1 W = (x~, K^{-1} r~)  */
-  double precond_floor;    /* Jacobi: |H_ii - theta| floored at this value; default 0.1             */
+  double precond_floor;    /* Jacobi: |H_ii - theta| floored at this value; default 2.0 (two level  */
+                           /* spacings of the CI spectrum: 0.1 amplifies near-degenerate rows)      */
   int cheb_degree;         /* ChebFSI polynomial degree d (Alg. 3); default 10 (Sec. 3.2)           */
   double lambda_ub;        /* ChebFSI spectrum upper bound; 0 = ten Lanczos steps (Sec. 3.2)        */
   int lanczos_maxbasis;    /* Lanczos / block Lanczos basis vectors before giving up; default 600   */
@@ -244,6 +245,10 @@ typedef struct {
   int rmm_fallback;        /* hybrid: when RMM-DIIS ends unconverged or with two collinear vectors, */
                            /* finish with LOBPCG on FP64 vectors from its result (default 1; 0 =   */
                            /* the paper's hybrid as printed, which has no remedy for that case)    */
+  double diis_tol;         /* RMM-DIIS least squares: drop the oldest history entry while a squared */
+                           /* Cholesky pivot of the normal matrix falls below diis_tol * its max   */
+                           /* diagonal; 0 = by the residual history's precision (1e-6 for FP32,    */
+                           /* 1e-13 for FP64)                                                       */
 } eig_opts;
 
 typedef struct {

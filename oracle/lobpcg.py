@@ -21,7 +21,7 @@ from .result import EigResult
 from .spmm import sym_upper_matmul, to_scipy_upper
 
 
-def lobpcg(H, X0, nev, tol=1e-6, maxiter=500, precond="jacobi", floor=0.1, U=None, stop=None,
+def lobpcg(H, X0, nev, tol=1e-6, maxiter=500, precond="jacobi", floor=2.0, U=None, stop=None,
            diagH=None):
     """stop(it, theta, relres) -> True ends the iteration early (used by the hybrid)."""
     U = to_scipy_upper(H) if U is None else U

@@ -67,7 +67,7 @@ def rr2(x, r, Hx, Hr):
         return float(A[0, 0] / B[0, 0]), np.array([1.0 / nx, 0.0])
 
 
-def rmmdiis(H, X0, tol=1e-6, maxiter=200, s_max=10, HX0=None, U=None, precond="none", floor=0.1):
+def rmmdiis(H, X0, tol=1e-6, maxiter=200, s_max=10, HX0=None, U=None, precond="none", floor=2.0):
     U = to_scipy_upper(H) if U is None else U
     diagH = U.diagonal()
     X0 = np.asarray(X0, dtype=np.float64)

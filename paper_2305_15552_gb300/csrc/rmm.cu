@@ -236,7 +236,8 @@ k_rmm_start(double* __restrict__ x, const double* __restrict__ hx, const double*
 // memory; each entry is computed with the same operations in the same order as a sequential
 // Cholesky would, so the result does not depend on the parallel layout.
 __global__ void __launch_bounds__(32) k_rmm_diis(const double* __restrict__ B, Window win,
-                                                 const int* __restrict__ active, int mp, double* __restrict__ alpha) {
+                                                 const int* __restrict__ active, int mp, double tol,
+                                                 double* __restrict__ alpha) {
   constexpr int M = kRmmSMax - 1;
   __shared__ double F[M][M + 1];
   __shared__ double rhs[M], y[M];
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(32) k_rmm_diis(const double* __restrict__ B, W
       if (lane == c) {
         double piv = F[c][c];
         for (int q = 0; q < c; ++q) piv -= F[c][q] * F[c][q];
-        if (!(piv > 1e-13 * mx)) fail = 1;
+        if (!(piv > tol * mx)) fail = 1;
         else F[c][c] = sqrt(piv);
       }
       __syncwarp();
@@ -403,8 +404,9 @@ eig_status rmm_start(double* x, const double* hx, const double* num, const doubl
   return EIG_OK;
 }
 
-eig_status rmm_diis(const double* B, Window win, const int* active, int mp, double* alpha, cudaStream_t st) {
-  k_rmm_diis<<<mp, 32, 0, st>>>(B, win, active, mp, alpha);
+eig_status rmm_diis(const double* B, Window win, const int* active, int mp, double* alpha, cudaStream_t st,
+                    double tol) {
+  k_rmm_diis<<<mp, 32, 0, st>>>(B, win, active, mp, tol, alpha);
   EIG_LAUNCH_CHECK("k_rmm_diis");
   return EIG_OK;
 }

@@ -54,7 +54,10 @@ eig_status rmm_start(double* x, const double* hx, const double* num, const doubl
 // Cholesky of the (s-1)x(s-1) normal matrix of the residual differences, dropping the oldest
 // entries while it is numerically singular.  B: [mp][kRmmSMax][kRmmSMax] Gram of the residual
 // history by slot.  Inactive columns get alpha = one-hot on the newest slot.
-eig_status rmm_diis(const double* B, Window win, const int* active, int mp, double* alpha, cudaStream_t st);
+// tol: an entry is dropped while a squared Cholesky pivot falls below tol * max diag (the normal
+// matrix is only as accurate as the residual history it is built from).
+eig_status rmm_diis(const double* B, Window win, const int* active, int mp, double* alpha, cudaStream_t st,
+                    double tol = 1e-13);
 
 // B[j][slot_new][slot_i] = B[j][slot_i][slot_new] = sums[j][1 + i] for i < win.s (sums: [mp][1+kRmmSMax]).
 eig_status rmm_store_gram(double* B, const double* sums, Window win_after, int slot_new, int mp, cudaStream_t st);

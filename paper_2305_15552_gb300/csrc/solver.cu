@@ -243,10 +243,6 @@ eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, st
   double* Xp = h->tmp64a.as<double>();
   double* HXp = h->tmp64b.as<double>();
   EIG_TRY(pad_columns(X, m, Xp, mp, n, c.st));
-  if (h->plan.val_type == EIG_BF16) {
-    // FP64 products with bf16 values are not instantiated; use the FP32-vector SpMM on hi/lo parts
-    return EIG_EUNSUPPORTED;
-  }
   EIG_TRY(spmm_run(&h->plan, Xp, HXp, mp, EIG_F64, c.st));
   const int grid = num_sms() * 4;
   DevBuf tmp;
@@ -458,7 +454,6 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
   const int64_t n = h->n;
   const int smax = std::max(1, std::min(c.o.s_max, kRmmSMax));
   if (mp > 32) return EIG_EUNSUPPORTED;
-  if (h->plan.val_type == EIG_BF16) return EIG_EUNSUPPORTED;
   const size_t slab = (size_t)n * mp;
   // big: x history (double-float), r history (FP32), x~ (double-float), r_raw, w, Hw (FP32),
   // and the FP64 start block and its product
@@ -552,7 +547,7 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
     Window win;
     win.s = std::min(count, smax);
     for (int i = 0; i < win.s; ++i) win.slot[i] = ((newest - (win.s - 1 - i)) % smax + smax) % smax;
-    EIG_TRY(rmm_diis(B, win, active, mp, alpha, c.st));
+    EIG_TRY(rmm_diis(B, win, active, mp, alpha, c.st, c.o.diis_tol > 0.0 ? c.o.diis_tol : 1e-6));
     EIG_TRY(rmx_coef(alpha, thh, sg, win, newest, mp, coef, c.st));
     const double* tref = thh + (size_t)newest * mp;
     int np = 0;
@@ -644,7 +639,6 @@ eig_status run_rmmdiis(Ctx& c, const double* X0, int maxiter, int* iters, bool* 
   // x^(0): normalise, accurate H x^(0) in FP64 vectors, theta^(0), r^(0) (Alg. 4 lines 2-4)
   EIG_TRY(pad_columns(X0, nev, xt, mp, n, c.st));
   EIG_TRY(col_sumsq(xt, mp, n, EIG_F64, xn2, cpart, c.st));
-  if (h->plan.val_type == EIG_BF16) return EIG_EUNSUPPORTED;
   EIG_TRY(c.spmm(xt, hxt, mp, EIG_F64, nev));
   {
     const int threads = (256 / mp) * mp;
@@ -693,7 +687,7 @@ eig_status run_rmmdiis(Ctx& c, const double* X0, int maxiter, int* iters, bool* 
     Window win;
     win.s = std::min(count, smax);
     for (int i = 0; i < win.s; ++i) win.slot[i] = ((newest - (win.s - 1 - i)) % smax + smax) % smax;
-    EIG_TRY(rmm_diis(B, win, active, mp, alpha, c.st));
+    EIG_TRY(rmm_diis(B, win, active, mp, alpha, c.st, c.o.diis_tol > 0.0 ? c.o.diis_tol : (vt == EIG_F32 ? 1e-6 : 1e-13)));
     int np = 0;
     EIG_TRY(rmm_combine(xh, rh, thh, alpha, win, thh + newest * mp, active, mp, n, vt, xt, hxt, rt, part, &np, c.st));
     EIG_TRY(reduce_partials(part, np, mp * 5, sums, c.st));
@@ -779,7 +773,7 @@ void eig_default_opts(eig_opts* o) {
   o->vec_type = EIG_F32;
   o->precond = 1;
   o->rmm_precond = 0;
-  o->precond_floor = 0.1;
+  o->precond_floor = 2.0;
   o->cheb_degree = 10;
   o->lambda_ub = 0.0;
   o->lanczos_maxbasis = 600;
@@ -791,6 +785,7 @@ void eig_default_opts(eig_opts* o) {
   o->timing = 0;
   o->rmm_maxiter = 0;
   o->rmm_fallback = 1;
+  o->diis_tol = 0.0;
   o->stream = nullptr;
 }
 

@@ -539,6 +539,7 @@ eig_status spmm_run_with_scratch(SpmmPlan* P, const void* X, void* Y, int nb, ei
     double* z = static_cast<double*>(scratch);
     if (P->val_type == EIG_F64) return dispatch_nb<double, double>(P, x, y, z, nb, st);
     if (P->val_type == EIG_F32) return dispatch_nb<double, float>(P, x, y, z, nb, st);
+    if (P->val_type == EIG_BF16) return dispatch_nb<double, uint16_t>(P, x, y, z, nb, st);
     return EIG_EUNSUPPORTED;
   }
   return EIG_EINVAL;

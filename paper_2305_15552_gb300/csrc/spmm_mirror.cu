@@ -819,5 +819,6 @@ EIG_MIRROR_INST(float, float)
 EIG_MIRROR_INST(float, uint16_t)
 EIG_MIRROR_INST(double, double)
 EIG_MIRROR_INST(double, float)
+EIG_MIRROR_INST(double, uint16_t)
 
 }  // namespace eig

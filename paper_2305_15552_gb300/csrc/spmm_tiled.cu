@@ -450,5 +450,6 @@ EIG_TILED_INST(float, float)
 EIG_TILED_INST(float, uint16_t)
 EIG_TILED_INST(double, double)
 EIG_TILED_INST(double, float)
+EIG_TILED_INST(double, uint16_t)
 
 }  // namespace eig

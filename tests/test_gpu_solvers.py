@@ -240,3 +240,15 @@ def test_hybrid_fallback_when_rmmdiis_stops_early(H3000f):
     rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type="f32", switch_after=1, rmm_maxiter=3, rmm_precond=1,
                      rmm_fallback=0)
     assert rc == binding.EIG_ENOT_CONVERGED and st["iterations_fallback"] == 0, st
+
+
+@pytest.mark.parametrize("vt", ["f32", "f64"])
+def test_hybrid_bf16_values(vt):
+    """BF16 matrix values (rounded at generation; the oracle solves that rounded matrix in FP64):
+    FP32 or FP64 vectors, certification through the BF16 x FP64 product."""
+    H = ci_matrix(3000, 100, 64, seed=1, storage="bf16")
+    lam, _ = O.lowest_eigpairs(O.to_dense(H), 5)
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type=vt, rmm_precond=1)
+    assert rc == 0, st
+    check_result(H, S, lam[:5])

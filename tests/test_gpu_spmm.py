@@ -60,7 +60,7 @@ def _check(H, nb, dtype, seed=0, R=0, Cb=0, layout="auto", misalign=False):
 @pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("nb", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("storage,dtype", [("f32", torch.float32), ("f64", torch.float64), ("f32", torch.float64),
-                                            ("bf16", torch.float32)])
+                                            ("bf16", torch.float32), ("bf16", torch.float64)])
 def test_ci_ragged(nb, storage, dtype, layout):
     H = ci_matrix(5000 + 37, 100, 64, seed=1, storage=storage)
     _check(H, nb, dtype, layout=layout)
