@@ -204,23 +204,51 @@ struct Carve {
 // ---------------------------------------------------------------------------------------
 // certification: true FP64 residuals of (theta_j, x_j) for the returned pairs
 // ---------------------------------------------------------------------------------------
+// Gram of the first m columns of X (n x ld, FP64) for the duplicate check: the m(m+1)/2 pairs
+// are spread over the CTA's threads (sets of `npairs` threads take interleaved rows), FP64 sums,
+// fixed-order reductions.  part: [cta][npairs].
+__global__ void k_pair_gram(const double* __restrict__ X, int m, int ld, int64_t n, double* __restrict__ part) {
+  __shared__ double red[256];
+  const int npairs = m * (m + 1) / 2;
+  const int sets = blockDim.x / npairs;
+  const int p = threadIdx.x % npairs, set = threadIdx.x / npairs;
+  int i = 0, j = p;
+  while (j >= m - i) { j -= m - i; ++i; }
+  j += i;
+  double acc = 0.0;
+  if (set < sets)
+    for (int64_t r = blockIdx.x * (int64_t)sets + set; r < n; r += (int64_t)gridDim.x * sets)
+      acc = fma(X[r * ld + i], X[r * ld + j], acc);
+  red[threadIdx.x] = (set < sets) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < npairs) {
+    double t = 0.0;
+    for (int q = 0; q < sets; ++q) t += red[q * npairs + threadIdx.x];
+    part[(size_t)blockIdx.x * npairs + threadIdx.x] = t;
+  }
+}
+
 // Two columns of X (n x ld, FP64, first m used) that are collinear (|cos| >= 0.9) with Ritz values
 // equal to 1e-6 relative: RMM-DIIS does not orthogonalise its vectors (Sec. 3.3).
 eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::vector<double>& theta,
                            bool* duplicate) {
   *duplicate = false;
   if (m < 2) return EIG_OK;
+  const int npairs = m * (m + 1) / 2;
+  if (npairs > 256) return EIG_OK;  // n_ev > 22: no check
+  const int grid = num_sms() * 4;
   DevBuf gbuf;
-  EIG_TRY(gbuf.reserve((size_t)ld * ld * 8 + gram_scratch_bytes(1, ld)));
-  double* G = gbuf.as<double>();
-  BlockList bl;
-  bl.n = 1;
-  bl.p[0] = X;
-  const int pa = 0, pb = 0;
-  EIG_TRY(gram_multi(bl, &pa, &pb, 1, ld, c.h->n, EIG_F64, G, G + (size_t)ld * ld, c.st));
-  std::vector<double> hg((size_t)ld * ld);
-  EIG_CUDA_TRY(cudaMemcpyAsync(hg.data(), G, hg.size() * 8, cudaMemcpyDeviceToHost, c.st));
+  EIG_TRY(gbuf.reserve((size_t)grid * npairs * 8 + (size_t)npairs * 8));
+  double* part = gbuf.as<double>();
+  double* Gp = part + (size_t)grid * npairs;
+  k_pair_gram<<<grid, 256, 0, c.st>>>(X, m, ld, c.h->n, part);
+  EIG_LAUNCH_CHECK("k_pair_gram");
+  EIG_TRY(reduce_partials(part, grid, npairs, Gp, c.st));
+  std::vector<double> hp(npairs), hg((size_t)ld * ld, 0.0);
+  EIG_CUDA_TRY(cudaMemcpyAsync(hp.data(), Gp, npairs * 8, cudaMemcpyDeviceToHost, c.st));
   EIG_TRY(c.sync());
+  for (int i = 0, q = 0; i < m; ++i)
+    for (int j = i; j < m; ++j, ++q) hg[(size_t)i * ld + j] = hg[(size_t)j * ld + i] = hp[q];
   for (int i = 0; i < m; ++i)
     for (int j = i + 1; j < m; ++j) {
       const double gi = hg[(size_t)i * ld + i], gj = hg[(size_t)j * ld + j];
