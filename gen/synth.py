@@ -265,3 +265,20 @@ def pad_rows(X: np.ndarray, n: int) -> np.ndarray:
     out = np.zeros((n, X.shape[1]), dtype=X.dtype)
     out[: X.shape[0]] = X
     return out
+
+
+def family_perturbation(H0: CSRUpper, seed: int, sigma: float = 0.1) -> np.ndarray:
+    """Values of a symmetric perturbation V on the stored pattern of H0 (diagonal included),
+    N(0, sigma^2), float64, one per stored entry of H0's upper triangle."""
+    ss = np.random.SeedSequence([int(seed), H0.n, H0.nnz, 0x7F4A])
+    rng = np.random.Generator(np.random.Philox(ss))
+    return sigma * rng.standard_normal(H0.nnz)
+
+
+def family_member(H0: CSRUpper, V: np.ndarray, g: float, storage: str = None) -> CSRUpper:
+    """H(g) = H0 + g V on H0's pattern, values rounded to `storage` (default: H0's)."""
+    st = storage or H0.storage
+    val = round_to_storage(H0.values_f64() + float(g) * np.asarray(V, dtype=np.float64), st)
+    meta = dict(H0.meta)
+    meta.update(kind="family", g=float(g))
+    return CSRUpper(n=H0.n, rowptr=H0.rowptr, col=H0.col, val=val, storage=st, meta=meta)

@@ -12,7 +12,9 @@ Layers
     eigenpairs (numpy eigh), Gram, CholQR2, Rayleigh-Ritz;
   * the paper's algorithms step by step: Lanczos (Sec. 2.1), block Lanczos (Alg. 1),
     LOBPCG (Alg. 2), ChebFSI (Alg. 3), RMM-DIIS (Alg. 4), hybrids (Sec. 4);
-  * certification helpers (true residuals, residual/Kato-Temple bounds).
+  * certification helpers (true residuals, residual/Kato-Temple bounds);
+  * the learned per-row preconditioner (oracle.learned): features, MLP forward/backward,
+    correction targets, loss and Adam step, in float64.
 
 Parity pins: every function is checked in tests/test_oracle_*.py against closed
 forms (Kronecker-sum Laplacian spectra, Chebyshev T_m(cos t) = cos(m t), 2x2 pencil
