@@ -223,8 +223,11 @@ typedef struct {
   eig_dtype vec_type;      /* vector precision of the SpMM operands and front-phase blocks:         */
                            /* EIG_F32 (default, FP64 kept for Grams/projected problems/DIIS and the */
                            /* RMM-DIIS iterates) or EIG_F64 (every vector in FP64)                  */
-  int precond;             /* LOBPCG K^{-1} of Eq. (wblock): 0 none, 1 Jacobi (default)              */
+  int precond;             /* LOBPCG K^{-1} of Eq. (wblock): 0 none, 1 Jacobi (default), 2 learned */
+                           /* (eig_lp_*, parameters in lp_params)                                  */
   int rmm_precond;         /* RMM-DIIS: 0 W = (x~, r~) as Alg. 4 (default), 1 W = (x~, K^{-1} r~)  */
+                           /* with Jacobi K, 2 with the learned K (FP32 vectors; FP64 vectors use  */
+                           /* Jacobi)                                                               */
   double precond_floor;    /* Jacobi: |H_ii - theta| floored at this value; default 2.0 (two level  */
                            /* spacings of the CI spectrum: 0.1 amplifies near-degenerate rows)      */
   int cheb_degree;         /* ChebFSI polynomial degree d (Alg. 3); default 10 (Sec. 3.2)           */
@@ -249,6 +252,8 @@ typedef struct {
                            /* Cholesky pivot of the normal matrix falls below diis_tol * its max   */
                            /* diagonal; 0 = by the residual history's precision (1e-6 for FP32,    */
                            /* 1e-13 for FP64)                                                       */
+  const float* lp_params;  /* learned preconditioner (precond or rmm_precond = 2): host FP32 vector  */
+                           /* of EIG_LP_PARAMS entries (layout at eig_lp_param_count); NULL = none */
 } eig_opts;
 
 typedef struct {
@@ -271,6 +276,11 @@ typedef struct {
                            /* and Y written once                                                     */
   int trace_rows;          /* rows written to opts->trace                                           */
   int iterations_fallback; /* LOBPCG iterations of the hybrid's fallback (0 when not needed)        */
+  int precond_fallback;    /* learned preconditioner: 0 = used throughout; otherwise the (1-based)  */
+                           /* iteration at which Jacobi replaced it (a step that raised the sum of */
+                           /* the wanted Ritz values, or a non-finite m r): LOBPCG in the low 16   */
+                           /* bits, RMM-DIIS in the high 16 bits                                    */
+  int64_t lp_spmm_calls;   /* products H r spent on the learned preconditioner's features           */
 } eig_stats;
 
 /* Fills *o with the defaults documented in eig_opts. */
@@ -299,6 +309,68 @@ EIG_API eig_status eig_solve(void* handle, eig_method method, const eig_opts* op
  * on_device = 0, device otherwise; may be NULL), relres[n_ev] (host; may be NULL).
  * EIG_EINVAL when no solve has produced a result yet. */
 EIG_API eig_status eig_ritz(void* handle, double* theta, double* X, double* relres, int on_device);
+
+/* ------------------------------------------------------------------------------------ *
+ * Learned per-row preconditioner (a replacement for K of Eq. (wblock))                 *
+ * ------------------------------------------------------------------------------------ *
+ * The paper leaves K open: it only has to approximate H (Sec. 2.3), and Secs. 5-6 name a
+ * better preconditioner as the way to cut iterations further.  The learned K^{-1} scales each
+ * residual entry, w_ij = m_ij r_ij, by m_ij = J_ij (1 + o_ij): J_ij = 1 / floor(H_ii - theta_j) is
+ * the Jacobi scale (|.| floored at 2, sign kept) and o_ij = MLP(f_ij) a learned correction, so a
+ * zero output layer is exactly the Jacobi K.  Six features of row i and column j:
+ *   f0 = H_ii, f1 = theta_j, f2 = H_ii - theta_j, f3 = (|H| 1)_i (absolute row sum of the full H),
+ *   f4 = sqrt(n) r_ij / ||r_j||, f5 = sqrt(n) ((H - D) r_j)_i / ||r_j||  (0 for a zero column).
+ * Network 6 -> 32 -> 32 -> 1, ReLU after both hidden layers, FP32, on u = (f - mu) / sigma.
+ * Parameter vector (FP32, EIG_LP_PARAMS entries, in this order):
+ *   mu[6] sigma[6] W1[32][6] b1[32] W2[32][32] b2[32] w3[32] b3
+ * mu and sigma are fixed feature statistics; the EIG_LP_TRAINED entries after them are trained.
+ * Where m r is not finite the entry takes the Jacobi value r / floor(H_ii - theta_j).
+ * Training target: the Jacobi-Davidson correction to first order measured against the
+ * converged wanted space X* (orthonormal n x k): z_j = x_j - X* p / (p^T p), p = X*^T x_j; loss
+ * L = (1/|J|) sum_{j in J} sum_i (m_ij r_ij - z_ij)^2 / ||z_j||^2 over the columns J with a
+ * target. */
+#define EIG_LP_PARAMS 1325
+#define EIG_LP_TRAINED 1313
+
+/* Number of entries of a parameter vector (EIG_LP_PARAMS). */
+EIG_API int eig_lp_param_count(void);
+
+/* One training sample from the solver's matrix.  X (device FP64 n x m row-major, m <= 32) and
+ * theta (host FP64 [m]) are Ritz pairs of H; the call forms R = H X - X diag(theta) and H R with
+ * the handle's SpMM plan and writes, all on the device:
+ *   F[(i*m + j)*6 + q] (FP32 features), r[i*m + j] (FP32 residual), z[i*m + j] (FP32 target),
+ *   colw[j] (FP64 weight of column j in the loss: 1 / (|J| ||z_j||^2), or 0 without a target).
+ * target 0: the correction target against Xstar (device FP64 n x k row-major, 1 <= k <= 32,
+ * orthonormal); target 1: the Jacobi target z = r / floor(H_ii - theta_j) (Xstar unused),
+ * used to start a network from Jacobi.  floor: the Jacobi floor (eig_opts.precond_floor).
+ * Synchronises stream.  Errors: EIG_EINVAL (sizes, null pointers). */
+EIG_API eig_status eig_lp_sample(void* handle, const double* X, int m, const double* theta, const double* Xstar,
+                                 int k, int target, double floor, float* F, float* r, float* z, double* colw,
+                                 void* stream);
+
+/* W = K^{-1} R with the learned K (params: host FP32 vector).  R, W: device n x m row-major of
+ * vec_type (EIG_F32 or EIG_F64), m a power of two <= 32, W may equal R; theta host FP64 [m].
+ * One SpMM of R with the handle's plan forms f5.  Synchronises stream. */
+EIG_API eig_status eig_lp_apply(void* handle, const float* params, const void* R, int m, eig_dtype vec_type,
+                                const double* theta, double floor, void* W, void* stream);
+
+/* m_out[e] = MLP(F[e*6 .. e*6+5]) for e < count (device FP32 in and out; params host FP32). */
+EIG_API eig_status eig_lp_forward(const float* params, const float* F, int64_t count, float* m_out, void* stream);
+
+/* Device scratch bytes eig_lp_grad needs. */
+EIG_API size_t eig_lp_grad_workspace_bytes(void);
+
+/* Loss and gradient of one sample (F, r, z, colw from eig_lp_sample; n rows, m columns):
+ * grad (device FP64 [EIG_LP_TRAINED + 1]) receives dL/d(params[12 + q]) for q < EIG_LP_TRAINED,
+ * then L.  params: device FP32 vector.  Deterministic (fixed-order reductions). */
+EIG_API eig_status eig_lp_grad(const float* params, const float* F, const float* r, const float* z,
+                               const double* colw, int64_t n, int m, double* grad, void* workspace, void* stream);
+
+/* One Adam step (Kingma & Ba) on the trained entries of params (device FP32) from grad
+ * (eig_lp_grad); m1, m2: device FP32 moment vectors of EIG_LP_PARAMS entries (start at zero);
+ * t: 1-based step count of the bias corrections. */
+EIG_API eig_status eig_lp_adam(float* params, const double* grad, float* m1, float* m2, int t, double lr,
+                               double beta1, double beta2, double eps, void* stream);
 
 #ifdef __cplusplus
 }

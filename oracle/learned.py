@@ -18,9 +18,13 @@ the off-diagonal part of (H r_j)_i; the diagonal part is H_ii r_ij, already give
 and f4.  The two residual features are scaled to unit root-mean-square so that one
 network serves every residual size from the start of a solve to convergence.
 
-Network: 6 -> 32 -> 32 -> 1, ReLU after both hidden layers, linear output; u = (f - mu) /
-sigma with mu, sigma fixed (feature statistics of the training set).  A non-finite m r
-falls back to the Jacobi value r / floor(H_ii - theta_j) (oracle.precond).
+Network: 6 -> 32 -> 32 -> 1, ReLU after both hidden layers, linear output o; u = (f - mu) /
+sigma with mu, sigma fixed (feature statistics of the training set).  The network learns a
+correction of the Jacobi scale J = 1 / floor(f2) (magnitude floored at JACOBI_FLOOR = 2, sign
+kept, zero -> +2, as oracle.precond):
+    m = J (1 + o),
+so that a zero output layer is exactly the Jacobi K.  A non-finite m r falls back to the
+Jacobi value r / floor(H_ii - theta_j) with the solver's floor (oracle.precond).
 
 Flat parameter vector (float32 on the GPU, the order the C ABI documents):
     mu[6] sigma[6] | W1[32][6] b1[32] W2[32][32] b2[32] w3[32] b3
@@ -51,6 +55,14 @@ OFF_W3 = OFF_B2 + HIDDEN
 OFF_B3 = OFF_W3 + HIDDEN
 N_PARAMS = OFF_B3 + 1          # 1325
 N_FIXED = 12
+JACOBI_FLOOR = 2.0
+
+
+def jacobi_scale(f2):
+    """J = 1 / floor(f2): |f2| floored at JACOBI_FLOOR, sign kept, zero -> +JACOBI_FLOOR."""
+    f2 = np.asarray(f2, dtype=np.float64)
+    mag = np.maximum(np.abs(f2), JACOBI_FLOOR)
+    return 1.0 / np.where(f2 < 0, -mag, mag)
 
 
 def unpack(params):
@@ -111,27 +123,29 @@ def features(H, theta, R, U=None):
 
 
 def forward(params, F):
-    """m = MLP(standardise(F)) for F (..., 6); returns (m, cache for backward)."""
+    """m = J(f2) (1 + MLP(standardise(F))) for F (..., 6); returns (m, cache for backward)."""
     P = unpack(params)
-    u = (np.asarray(F, dtype=np.float64) - P["mu"]) / P["sigma"]
+    F = np.asarray(F, dtype=np.float64)
+    u = (F - P["mu"]) / P["sigma"]
     a1 = u @ P["W1"].T + P["b1"]
     h1 = np.maximum(a1, 0.0)
     a2 = h1 @ P["W2"].T + P["b2"]
     h2 = np.maximum(a2, 0.0)
-    m = h2 @ P["w3"] + P["b3"]
-    return m, dict(u=u, a1=a1, h1=h1, a2=a2, h2=h2)
+    o = h2 @ P["w3"] + P["b3"]
+    J = jacobi_scale(F[..., 2])
+    return J * (1.0 + o), dict(u=u, a1=a1, h1=h1, a2=a2, h2=h2, J=J)
 
 
 def backward(params, cache, dm):
     """Gradient of sum(dm * m) with respect to the flat parameters (the fixed mu, sigma get
-    zero).  Chain rule through the two ReLU layers; ReLU'(0) = 0."""
+    zero).  dm/do = J, then the chain rule through the two ReLU layers; ReLU'(0) = 0."""
     P = unpack(params)
     u = cache["u"].reshape(-1, N_FEAT)
     a1 = cache["a1"].reshape(-1, HIDDEN)
     h1 = cache["h1"].reshape(-1, HIDDEN)
     a2 = cache["a2"].reshape(-1, HIDDEN)
     h2 = cache["h2"].reshape(-1, HIDDEN)
-    g = np.asarray(dm, dtype=np.float64).reshape(-1)
+    g = (np.asarray(dm, dtype=np.float64) * cache["J"]).reshape(-1)
     dw3 = h2.T @ g
     db3 = g.sum()
     da2 = (g[:, None] * P["w3"][None, :]) * (a2 > 0)

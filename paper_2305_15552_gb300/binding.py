@@ -50,7 +50,7 @@ class Opts(C.Structure):
                 ("X0", C.c_void_p), ("x0_cols", C.c_int), ("x0_on_device", C.c_int), ("seed", C.c_uint64),
                 ("certify", C.c_int), ("timing", C.c_int), ("stream", C.c_void_p), ("trace", C.c_void_p),
                 ("trace_cap", C.c_int), ("rmm_maxiter", C.c_int), ("rmm_fallback", C.c_int),
-                ("diis_tol", C.c_double)]
+                ("diis_tol", C.c_double), ("lp_params", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -59,7 +59,7 @@ class Stats(C.Structure):
                 ("last_tau", C.c_double), ("max_relres", C.c_double), ("time_ms_total", C.c_double),
                 ("time_ms_spmm", C.c_double), ("time_ms_front", C.c_double), ("time_ms_rmm", C.c_double),
                 ("spmm_timed", C.c_int64), ("spmm_bytes", C.c_double), ("trace_rows", C.c_int),
-                ("iterations_fallback", C.c_int)]
+                ("iterations_fallback", C.c_int), ("precond_fallback", C.c_int), ("lp_spmm_calls", C.c_int64)]
 
 
 _SIGS = {
@@ -90,6 +90,17 @@ _SIGS = {
     "eig_destroy": (None, [C.c_void_p]),
     "eig_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Opts), C.POINTER(Stats)]),
     "eig_ritz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "eig_lp_param_count": (C.c_int, []),
+    "eig_lp_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "eig_lp_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double,
+                               C.c_void_p, C.c_void_p]),
+    "eig_lp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "eig_lp_grad_workspace_bytes": (C.c_size_t, []),
+    "eig_lp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                              C.c_void_p, C.c_void_p, C.c_void_p]),
+    "eig_lp_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                              C.c_double, C.c_double, C.c_void_p]),
 }
 
 
@@ -328,7 +339,13 @@ class Solver:
         o = Opts()
         self._lib.eig_default_opts(C.byref(o))
         keep = None
+        keep_lp = None
         for k, v in opts.items():
+            if k == "lp_params":
+                keep_lp = np.ascontiguousarray(v, dtype=np.float32)
+                assert keep_lp.shape == (N_LP_PARAMS,), keep_lp.shape
+                o.lp_params = keep_lp.ctypes.data_as(C.c_void_p).value
+                continue
             if k == "vec_type":
                 v = STORAGE[v] if isinstance(v, str) else v
             if k == "front":
@@ -354,7 +371,7 @@ class Solver:
         stats = Stats()
         rc = self._lib.eig_solve(self._h, METHODS[method] if isinstance(method, str) else int(method), C.byref(o),
                                  C.byref(stats))
-        del keep
+        del keep, keep_lp
         if rc not in (EIG_OK, EIG_ENOT_CONVERGED, EIG_EDUPLICATE):
             raise EigError(rc, "eig_solve")
         st = {k: getattr(stats, k) for k, _ in Stats._fields_}
@@ -376,6 +393,37 @@ class Solver:
             check(self._lib.eig_ritz(self._h, _ptr(th), _ptr(X), _ptr(rel), 0), "eig_ritz")
         return th, X, rel
 
+    def lp_sample(self, X, theta, Xstar=None, target=0, floor=2.0):
+        """eig_lp_sample: training sample of the learned preconditioner from Ritz pairs (X: torch
+        FP64 n x m on the device, theta: m values; Xstar: torch FP64 n x k, for target 0).  Returns a
+        dict of device tensors F (n*m x 6), r, z (n*m) FP32 and colw (m) FP64."""
+        import numpy as np
+        import torch
+        n, m = X.shape
+        assert X.dtype == torch.float64 and X.is_contiguous()
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        F = torch.empty(n * m, 6, dtype=torch.float32, device=X.device)
+        r = torch.empty(n * m, dtype=torch.float32, device=X.device)
+        z = torch.empty(n * m, dtype=torch.float32, device=X.device)
+        colw = torch.empty(m, dtype=torch.float64, device=X.device)
+        k = 0 if Xstar is None else int(Xstar.shape[1])
+        check(self._lib.eig_lp_sample(self._h, X.data_ptr(), m, _ptr(th), None if Xstar is None else Xstar.data_ptr(),
+                                      k, int(target), float(floor), F.data_ptr(), r.data_ptr(), z.data_ptr(),
+                                      colw.data_ptr(), stream_ptr()), "eig_lp_sample")
+        return dict(F=F, r=r, z=z, colw=colw, n=n, m=m)
+
+    def lp_apply(self, params, R, theta, floor=2.0, W=None):
+        """eig_lp_apply: W = K^{-1} R with the learned K (params: numpy FP32 vector)."""
+        import numpy as np
+        import torch
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        if W is None:
+            W = torch.empty_like(R)
+        check(self._lib.eig_lp_apply(self._h, _ptr(p), R.data_ptr(), int(R.shape[1]), vec_dtype(R), _ptr(th),
+                                     float(floor), W.data_ptr(), stream_ptr()), "eig_lp_apply")
+        return W
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.eig_destroy(self._h)
@@ -386,3 +434,43 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------------------
+# learned preconditioner: network kernels
+# ---------------------------------------------------------------------------------------
+N_LP_PARAMS = 1325
+N_LP_TRAINED = 1313
+
+
+def lp_forward(params, F):
+    """eig_lp_forward: m for the feature rows F (torch FP32 count x 6 on the device)."""
+    import numpy as np
+    import torch
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    out = torch.empty(F.shape[0], dtype=torch.float32, device=F.device)
+    check(load().eig_lp_forward(_ptr(p), F.data_ptr(), int(F.shape[0]), out.data_ptr(), stream_ptr()),
+          "eig_lp_forward")
+    return out
+
+
+def lp_grad(params_dev, sample, grad=None, workspace=None):
+    """eig_lp_grad on a sample from Solver.lp_sample; params_dev: torch FP32 vector on the device.
+    Returns the device FP64 vector [dL/dparams[12:], L]."""
+    import torch
+    lib = load()
+    dev = params_dev.device
+    if grad is None:
+        grad = torch.empty(N_LP_TRAINED + 1, dtype=torch.float64, device=dev)
+    if workspace is None:
+        workspace = torch.empty(lib.eig_lp_grad_workspace_bytes(), dtype=torch.uint8, device=dev)
+    check(lib.eig_lp_grad(params_dev.data_ptr(), sample["F"].data_ptr(), sample["r"].data_ptr(),
+                          sample["z"].data_ptr(), sample["colw"].data_ptr(), int(sample["n"]), int(sample["m"]),
+                          grad.data_ptr(), workspace.data_ptr(), stream_ptr()), "eig_lp_grad")
+    return grad
+
+
+def lp_adam(params_dev, grad, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """eig_lp_adam: one Adam step on params_dev (device FP32, in place)."""
+    check(load().eig_lp_adam(params_dev.data_ptr(), grad.data_ptr(), m1.data_ptr(), m2.data_ptr(), int(t),
+                             float(lr), float(beta1), float(beta2), float(eps), stream_ptr()), "eig_lp_adam")

@@ -86,6 +86,9 @@ eig_status rmx_coef(const double* alpha, const double* thh, const double* sg, Wi
 eig_status rmx_store_gram(double* B, const double* sums, const double* sg, Window win_after, int slot_new, int mp,
                           cudaStream_t st);
 // w = K^{-1}(H x~ - theta~ x~) (Jacobi, floored) from the combine sums [mp][3].
+// r~ = r_raw - mu x~ (FP32 n x mp, zero on inactive columns) and theta~ = theta_ref + mu (mp).
+eig_status rmx_shifted(const void* xt, const float* rraw, const double* sums, const double* theta_ref,
+                       const int* active, int mp, int64_t n, float* rt, double* theta_out, cudaStream_t st);
 eig_status rmx_precond(const void* xt, const float* rraw, const double* sums, const double* theta_ref,
                        const int* active, const double* diagH, double floor_, int mp, int64_t n, float* w,
                        cudaStream_t st);

@@ -281,6 +281,43 @@ k_rmx_precond(const float2* __restrict__ xt, const float* __restrict__ rraw, con
   }
 }
 
+// The shifted residual r~ = r_raw - mu x~ of k_rmx_precond, materialised (FP32, zero on
+// inactive columns) for the learned preconditioner, and theta~ = theta_ref + mu.
+template <int C>
+__global__ void __launch_bounds__(kThreads)
+k_rmx_shifted(const float2* __restrict__ xt, const float* __restrict__ rraw, const double* __restrict__ sums,
+              const double* __restrict__ theta_ref, const int* __restrict__ active, int mp, int64_t n,
+              float* __restrict__ rt, double* __restrict__ theta_out) {
+  const int gpr = mp / C;
+  const int j0 = (threadIdx.x % gpr) * C;
+  float mu[C];
+  bool act[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int j = j0 + c;
+    const double xx = sums[j * 3 + 0];
+    const double m = xx > 0.0 ? sums[j * 3 + 1] / xx : 0.0;
+    mu[c] = (float)m;
+    act[c] = active[j] != 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < mp) {
+    const int j = threadIdx.x;
+    const double xx = sums[j * 3 + 0];
+    theta_out[j] = theta_ref[j] + (xx > 0.0 ? sums[j * 3 + 1] / xx : 0.0);
+  }
+  const int64_t ng = n * gpr;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = g / gpr;
+    const size_t e = (size_t)r * mp + j0;
+    float xh[C], xl[C], rv[C], ov[C];
+    DFv<C>::ld(xt + e, xh, xl);
+    F32v<C>::ld(rraw + e, rv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) ov[c] = act[c] ? rv[c] - mu[c] * xh[c] : 0.0f;
+    F32v<C>::st(rt + e, ov);
+  }
+}
+
 // Partials [cta][j][5] of <x~,w>, <w,w>, <w,r_raw>, <x~, Hw - theta_ref w>, <w, Hw - theta_ref w>.
 template <int C>
 __global__ void __launch_bounds__(kThreads)
@@ -556,6 +593,18 @@ eig_status rmx_precond(const void* xt, const float* rraw, const double* sums, co
     k_rmx_precond<C><<<grid, kThreads, 0, st>>>((const float2*)xt, rraw, sums, theta_ref, active, diagH, floor_, mp,
                                                 n, w);
     EIG_LAUNCH_CHECK("k_rmx_precond");
+    return EIG_OK;
+  });
+}
+
+eig_status rmx_shifted(const void* xt, const float* rraw, const double* sums, const double* theta_ref,
+                       const int* active, int mp, int64_t n, float* rt, double* theta_out, cudaStream_t st) {
+  const int grid = rmx_grid(n, mp);
+  return by_cols(mp, [&](auto tag) {
+    constexpr int C = decltype(tag)::value;
+    k_rmx_shifted<C><<<grid, kThreads, 0, st>>>((const float2*)xt, rraw, sums, theta_ref, active, mp, n, rt,
+                                                theta_out);
+    EIG_LAUNCH_CHECK("k_rmx_shifted");
     return EIG_OK;
   });
 }

@@ -13,6 +13,7 @@
 #include "rmm.cuh"
 #include "small.cuh"
 #include "solver.cuh"
+#include "learned.cuh"
 #include "spmm.cuh"
 
 namespace eig {
@@ -201,6 +202,21 @@ struct Carve {
   bool bad = false;
 };
 
+// Learned K^{-1} (precond / rmm_precond = 2) on the residual block R (n x ld, first m columns),
+// written to W (may alias R): one SpMM for H R into HR (scratch), then the fused feature + MLP
+// kernel.  theta, rsq: device FP64 [m]; active may be null.
+static eig_status lp_precondition(Ctx& c, const void* R, void* HR, int ld, int m, eig_dtype vt, const double* theta,
+                                  const double* rsq, const int* active, int64_t spmv_cols, void* W, int* nonfinite) {
+  Handle* h = c.h;
+  EIG_TRY(lp_ensure_rowabs(h, c.st));
+  EIG_TRY(c.spmm(R, HR, ld, vt, spmv_cols));
+  c.s->lp_spmm_calls += 1;
+  LpParams prm;
+  std::memcpy(prm.p, c.o.lp_params, sizeof(prm.p));
+  return lp_apply(prm, R, HR, ld, m, h->n, vt, h->plan.diag.as<double>(), h->lp_rowabs.as<double>(), theta, rsq,
+                  c.o.precond_floor, active, W, nonfinite, c.st);
+}
+
 // ---------------------------------------------------------------------------------------
 // certification: true FP64 residuals of (theta_j, x_j) for the returned pairs
 // ---------------------------------------------------------------------------------------
@@ -336,6 +352,13 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   EIG_TRY(h->host.reserve((2 * nb + 8) * 8));
   double* hstat = h->host.as<double>();
   const double* diagH = h->plan.diag.as<double>();
+  // learned K^{-1} (precond = 2): the update forms plain residuals, lp_precondition scales them
+  bool lp_on = c.o.precond == 2;
+  if (lp_on && !c.o.lp_params) return EIG_EINVAL;
+  auto upd_precond = [&]() { return lp_on ? 0 : (c.o.precond ? 1 : 0); };
+  int* nonfin = reinterpret_cast<int*>(stat + 2 * nb + 1);
+  EIG_CUDA_TRY(cudaMemsetAsync(nonfin, 0, 4, c.st));
+  double lp_prev = 0.0;
   // X = X0 (FP64 n x x0_cols, x0_cols >= nb ... padded with random when fewer)
   EIG_TRY(h->tmp64a.reserve((size_t)n * nb * 8));
   double* X0p = h->tmp64a.as<double>();
@@ -376,9 +399,10 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
     std::swap(h->blk[3].p, h->blk[5].p);
     X = h->blk[0].p; P = h->blk[2].p; HX = h->blk[3].p; HP = h->blk[5].p;
     int np = 0;
-    EIG_TRY(lobpcg_update(X, W, P, HX, HW, HP, C, nb, nb, theta, diagH, c.o.precond_floor, c.o.precond, n, vt,
+    EIG_TRY(lobpcg_update(X, W, P, HX, HW, HP, C, nb, nb, theta, diagH, c.o.precond_floor, upd_precond(), n, vt,
                           upart, ugrid, &np, c.st));
     EIG_TRY(reduce_partials(upart, np, nb, rsq, c.st));
+    if (lp_on) EIG_TRY(lp_precondition(c, W, HW, nb, nb, vt, theta, rsq, nullptr, nb, W, nonfin));
     EIG_CUDA_TRY(cudaMemcpyAsync(hstat, stat, (2 * nb + 8) * 8, cudaMemcpyDeviceToHost, c.st));
     EIG_TRY(c.sync());
     if (*reinterpret_cast<int*>(hstat + 2 * nb) != SMALL_OK) return EIG_EBREAKDOWN;
@@ -392,6 +416,7 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   };
   read_status();
   c.trace(0, 0, th.data(), rel.data(), nev);
+  for (int j = 0; j < nev; ++j) lp_prev += th[j];
   bool conv = true;
   for (int j = 0; j < nev; ++j) conv = conv && rel[j] < c.o.tol;
   int it = 0;
@@ -453,13 +478,26 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
       break;
     }
     int nparts = 0;
-    EIG_TRY(lobpcg_update(X, W, P, HX, HW, HP, C, k, nb, theta, diagH, c.o.precond_floor, c.o.precond, n, vt, upart,
+    EIG_TRY(lobpcg_update(X, W, P, HX, HW, HP, C, k, nb, theta, diagH, c.o.precond_floor, upd_precond(), n, vt, upart,
                           ugrid, &nparts, c.st));
     EIG_TRY(reduce_partials(upart, nparts, nb, rsq, c.st));
-    EIG_CUDA_TRY(cudaMemcpyAsync(hstat, stat, (2 * nb) * 8, cudaMemcpyDeviceToHost, c.st));
+    if (lp_on) EIG_TRY(lp_precondition(c, W, HW, nb, nb, vt, theta, rsq, nullptr, nb, W, nonfin));
+    EIG_CUDA_TRY(cudaMemcpyAsync(hstat, stat, (2 * nb + 2) * 8, cudaMemcpyDeviceToHost, c.st));
     EIG_TRY(c.sync());
     hasP = true;
     read_status();
+    if (lp_on) {
+      // Jacobi replaces the learned K once a step raised the wanted Ritz values' sum or an
+      // entry of m r was not finite
+      double sum = 0.0;
+      for (int j = 0; j < nev; ++j) sum += th[j];
+      const int bad = *reinterpret_cast<const int*>(hstat + 2 * nb + 1);
+      if (bad > 0 || (it > 1 && sum > lp_prev + 1e-6 * std::max(1.0, std::fabs(lp_prev)))) {
+        lp_on = false;
+        c.s->precond_fallback |= std::min(it, 0xFFFF);
+      }
+      lp_prev = sum;
+    }
     c.trace(0, it, th.data(), rel.data(), nev);
     conv = true;
     for (int j = 0; j < nev; ++j) conv = conv && rel[j] < c.o.tol;
@@ -485,7 +523,12 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
   const size_t slab = (size_t)n * mp;
   // big: x history (double-float), r history (FP32), x~ (double-float), r_raw, w, Hw (FP32),
   // and the FP64 start block and its product
-  const size_t big_bytes = smax * slab * 8 + smax * slab * 4 + slab * 8 + 3 * slab * 4 + 2 * slab * 8 + 8 * 256;
+  // learned K^{-1} of the corrections (rmm_precond = 2): one more FP32 block for r~
+  const bool lp_req = c.o.rmm_precond == 2;
+  if (lp_req && !c.o.lp_params) return EIG_EINVAL;
+  bool lp_on = lp_req;
+  const size_t big_bytes = smax * slab * 8 + smax * slab * 4 + slab * 8 + 3 * slab * 4 + 2 * slab * 8 + 8 * 256 +
+                           (lp_req ? slab * 4 + 256 : 0);
   EIG_TRY(h->big.reserve(big_bytes));
   Carve bc(h->big.p, h->big.bytes);
   float2* xh = bc.take<float2>(smax * slab);
@@ -496,11 +539,12 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
   float* hw = bc.take<float>(slab);
   double* xs = bc.take<double>(slab);
   double* hxs = bc.take<double>(slab);
+  float* rt = lp_req ? bc.take<float>(slab) : nullptr;
   const int grid = std::max(rmx_grid(n, mp), rmm_grid(n, mp));
   const size_t small_bytes = (size_t)mp * kRmmSMax * kRmmSMax * 8 + mp * kRmmSMax * 8 + mp * 3 * kRmmSMax * 4 +
                              mp * 5 * 8 + mp * 8 * 2 + mp * 4 + 2 * kRmmSMax * mp * 8 + mp * 8 +
                              (size_t)grid * mp * (1 + kRmmSMax) * 8 + mp * (1 + kRmmSMax) * 8 * 3 +
-                             colsum_scratch_bytes(mp) + 16 * 256;
+                             colsum_scratch_bytes(mp) + 16 * 256 + mp * 16 + 3 * 256;
   EIG_TRY(h->small.reserve(small_bytes));
   Carve cv(h->small.p, h->small.bytes);
   double* B = cv.take<double>((size_t)mp * kRmmSMax * kRmmSMax);
@@ -517,9 +561,13 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
   double* s1 = cv.take<double>((size_t)mp * (1 + kRmmSMax));
   double* s2 = cv.take<double>((size_t)mp * (1 + kRmmSMax));
   void* cpart = cv.take<unsigned char>(colsum_scratch_bytes(mp));
+  double* th_t = cv.take<double>(mp);
+  double* rsq_t = cv.take<double>(mp);
+  int* nonfin = cv.take<int>(2);
   if (!bc.ok() || !cv.ok()) return EIG_EUNSUPPORTED;
   EIG_TRY(h->host.reserve(mp * 2 * 8 + 64));
   double* hstat = h->host.as<double>();
+  EIG_CUDA_TRY(cudaMemsetAsync(nonfin, 0, 8, c.st));
   EIG_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)mp * kRmmSMax * kRmmSMax * 8, c.st));
   // x^(0): accurate H x^(0) (double-float SpMM), theta^(0), r^(0) (Alg. 4 lines 2-4)
   EIG_TRY(pad_columns(X0, nev, xs, mp, n, c.st));
@@ -582,10 +630,15 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
     EIG_TRY(rmx_combine(xh, rh, coef, win, newest, active, mp, n, xt, rraw, c.o.rmm_precond ? nullptr : w, part, &np,
                         c.st));
     EIG_TRY(reduce_partials(part, np, mp * 3, s1, c.st));
-    if (c.o.rmm_precond)
-      EIG_TRY(rmx_precond(xt, rraw, s1, tref, active, h->plan.diag.as<double>(), c.o.precond_floor, mp, n, w, c.st));
     int nact = 0;
     for (int j = 0; j < mp; ++j) nact += act[j];
+    if (lp_on) {
+      EIG_TRY(rmx_shifted(xt, rraw, s1, tref, active, mp, n, rt, th_t, c.st));
+      EIG_TRY(col_sumsq(rt, mp, n, EIG_F32, rsq_t, cpart, c.st));
+      EIG_TRY(lp_precondition(c, rt, hw, mp, mp, EIG_F32, th_t, rsq_t, active, nact, w, nonfin));
+    } else if (c.o.rmm_precond) {
+      EIG_TRY(rmx_precond(xt, rraw, s1, tref, active, h->plan.diag.as<double>(), c.o.precond_floor, mp, n, w, c.st));
+    }
     EIG_TRY(c.spmm(w, hw, mp, EIG_F32, nact));
     EIG_TRY(rmx_dots(xt, w, rraw, hw, tref, mp, n, part, &np, c.st));
     EIG_TRY(reduce_partials(part, np, mp * 5, s2, c.st));
@@ -600,11 +653,25 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
     std::vector<double> hs((size_t)mp * (1 + wa.s));
     EIG_CUDA_TRY(cudaMemcpyAsync(hs.data(), sums, hs.size() * 8, cudaMemcpyDeviceToHost, c.st));
     EIG_CUDA_TRY(cudaMemcpyAsync(hstat, theta, mp * 8, cudaMemcpyDeviceToHost, c.st));
+    if (lp_on) EIG_CUDA_TRY(cudaMemcpyAsync(hstat + 2 * mp, nonfin, 4, cudaMemcpyDeviceToHost, c.st));
     EIG_TRY(c.sync());
     for (int j = 0; j < mp; ++j) hstat[mp + j] = hs[(size_t)j * (1 + wa.s)];
     ++count;
     newest = slot_new;
+    const double prev_sum = lp_on ? [&]() { double t = 0.0; for (int j = 0; j < nev; ++j) t += th[j]; return t; }()
+                                  : 0.0;
     done = refresh();
+    if (lp_on) {
+      // Jacobi replaces the learned K once a step raised the wanted Ritz values' sum or an
+      // entry of m r was not finite
+      double sum = 0.0;
+      for (int j = 0; j < nev; ++j) sum += th[j];
+      const int bad = *reinterpret_cast<const int*>(hstat + 2 * mp);
+      if (bad > 0 || sum > prev_sum + 1e-6 * std::max(1.0, std::fabs(prev_sum))) {
+        lp_on = false;
+        c.s->precond_fallback |= std::min(it, 0xFFFF) << 16;
+      }
+    }
     c.trace(1, it, th.data(), rel.data(), nev);
   }
   *iters = it;
@@ -886,6 +953,9 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
     EIG_CUDA_TRY(cudaEventCreate(&t2));
     EIG_CUDA_TRY(cudaEventRecord(t0, c.st));
   }
+  // certified residuals the hybrid already computed for its fallback decision (reused below)
+  std::vector<double> pre_rel;
+  bool pre_dup = false, have_pre = false;
   auto front_then_rmm = [&](eig_method front) -> eig_status {
     std::vector<double> prev;
     double best_rel = INFINITY;
@@ -961,12 +1031,22 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
                         &theta));
     c.s->iterations_rmm = rit;
     bool dup = false;
-    if (c.o.rmm_fallback) EIG_TRY(find_duplicates(c, h->Xres.as<double>(), nev, nev, theta, &dup));
+    if (c.o.rmm_fallback) {
+      // RMM-DIIS updates its residuals by recurrence; over many iterations in FP32 that estimate
+      // drifts from H x - theta x, so the FP64 residuals decide whether it converged
+      theta.resize(nev);
+      EIG_TRY(certify(c, h->Xres.as<double>(), theta, &pre_rel, &dup));
+      for (double r : pre_rel) conv = conv && r <= c.o.tol;
+      pre_dup = dup;
+      have_pre = conv && !dup;
+    }
     if (c.o.rmm_fallback && (!conv || dup)) {
       // LOBPCG on FP64 vectors (a subspace method: it separates what RMM-DIIS let drift together)
       // from the RMM-DIIS vectors, to the requested tolerance
       const eig_dtype vt_saved = c.o.vec_type;
+      const int pre_saved = c.o.precond;
       c.o.vec_type = EIG_F64;
+      if (c.o.precond == 2) c.o.precond = 1;   // the safety net runs with the Jacobi K
       int fit = 0, freason = 0;
       bool fc = false;
       DevBuf Xf2, X0f;
@@ -976,6 +1056,7 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
       const eig_status fr = run_lobpcg(c, X0f.as<double>(), nev, c.o.maxiter, StopFn(), &fit, &freason, &fc,
                                        Xf2.as<double>(), &theta);
       c.o.vec_type = vt_saved;
+      c.o.precond = pre_saved;
       EIG_TRY(fr);
       c.s->iterations_fallback = fit;
       BlockList in;
@@ -1059,7 +1140,10 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
   // true FP64 residuals of the returned pairs
   std::vector<double> rel;
   bool dup = false;
-  if (c.o.certify) {
+  if (have_pre) {
+    rel = pre_rel;
+    dup = pre_dup;
+  } else if (c.o.certify) {
     EIG_TRY(certify(c, h->Xres.as<double>(), h->theta, &rel, &dup));
   } else {
     rel.assign(nev, NAN);
@@ -1103,6 +1187,8 @@ eig_status eig_solve(void* handle, eig_method method, const eig_opts* opts, eig_
   if (!(o.tol > 0.0) || o.maxiter < 0 || o.s_max < 1 || o.s_max > kRmmSMax) return EIG_EINVAL;
   if (o.vec_type != EIG_F32 && o.vec_type != EIG_F64) return EIG_EINVAL;
   if (o.X0 && o.x0_cols < 1) return EIG_EINVAL;
+  if (o.precond < 0 || o.precond > 2 || o.rmm_precond < 0 || o.rmm_precond > 2) return EIG_EINVAL;
+  if ((o.precond == 2 || o.rmm_precond == 2) && !o.lp_params) return EIG_EINVAL;
   eig_stats local;
   std::memset(&local, 0, sizeof(local));
   Ctx c;

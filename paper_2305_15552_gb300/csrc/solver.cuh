@@ -39,6 +39,10 @@ struct Handle {
   DevBuf small;                // projected problems, partials
   DevBuf tmp64a, tmp64b;       // n x nb FP64 temporaries
   PinnedBuf host;
+  // learned preconditioner: (|H| 1)_i (computed on first use) and sample workspaces
+  DevBuf lp_rowabs;
+  bool lp_rowabs_ok = false;
+  DevBuf lp_buf[3], lp_small;
 };
 
 // Per-solve context
@@ -93,6 +97,8 @@ eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::ve
                            bool* duplicate);
 eig_status certify(Ctx& c, const double* X, const std::vector<double>& theta, std::vector<double>* relres,
                    bool* duplicate);
+// (|H| 1)_i of the handle's matrix into h->lp_rowabs (once per handle).
+eig_status lp_ensure_rowabs(Handle* h, cudaStream_t st);
 inline int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
 
 }  // namespace eig

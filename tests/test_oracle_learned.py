@@ -36,8 +36,13 @@ def test_row_abs_sum_brute_force():
     np.testing.assert_allclose(L.row_abs_sum(H), np.abs(D).sum(axis=1), rtol=1e-14, atol=1e-14)
 
 
+def test_jacobi_scale():
+    np.testing.assert_array_equal(L.jacobi_scale([0.0, 1.0, -1.5, 4.0, -8.0]), [0.5, 0.5, -0.5, 0.25, -0.125])
+
+
 def test_forward_closed_form_linear_network():
-    """Hidden units relu(u_k), relu(-u_k) recombined with +-c_k give m = c . u + b3 exactly."""
+    """Hidden units relu(u_k), relu(-u_k) recombined with +-c_k give o = c . u + b3 exactly, and
+    m = J(f2) (1 + o)."""
     rng = np.random.default_rng(0)
     mu, sg = rng.standard_normal(6), 0.5 + rng.random(6)
     c = rng.standard_normal(6)
@@ -49,7 +54,11 @@ def test_forward_closed_form_linear_network():
     p = L.pack(dict(mu=mu, sigma=sg, W1=W1, b1=np.zeros(32), W2=W2, b2=np.zeros(32), w3=w3, b3=0.25))
     F = rng.standard_normal((7, 3, 6)) * 3
     m, _ = L.forward(p, F)
-    np.testing.assert_allclose(m, ((F - mu) / sg) @ c + 0.25, rtol=1e-13, atol=1e-13)
+    J = 1.0 / np.where(F[..., 2] < 0, -1, 1) / np.maximum(np.abs(F[..., 2]), 2.0)
+    np.testing.assert_allclose(m, J * (1.0 + ((F - mu) / sg) @ c + 0.25), rtol=1e-13, atol=1e-13)
+    # zero output layer: exactly the Jacobi scale
+    p[L.OFF_W3:L.OFF_B3 + 1] = 0.0
+    np.testing.assert_array_equal(L.forward(p, F)[0], J)
 
 
 def _random_problem(seed=1, n=12, m=3):
@@ -90,16 +99,16 @@ def test_loss_zero_at_its_minimum():
 
 
 def test_loss_column_weighting():
-    """One column, m = b3 constant: L = sum((b3 r - z)^2) / ||z||^2."""
+    """One column, f2 = 0 (J = 1/2) and b3 = 1, so m = 1: L = sum((r - z)^2) / ||z||^2."""
     p = np.zeros(L.N_PARAMS)
     p[L.OFF_SIGMA:L.OFF_SIGMA + 6] = 1.0
-    p[L.OFF_B3] = 0.5
+    p[L.OFF_B3] = 1.0
     F = np.zeros((3, 1, 6))
     R = np.array([[2.0], [0.0], [-4.0]])
     Z = np.array([[1.0], [1.0], [1.0]])
     c = np.array([1.0 / (Z[:, 0] @ Z[:, 0])])
     val = L.loss(p, F, R, Z, c)[0]
-    assert val == pytest.approx(((1 - 1) ** 2 + (0 - 1) ** 2 + (-2 - 1) ** 2) / 3.0, rel=1e-15)
+    assert val == pytest.approx(((2 - 1) ** 2 + (0 - 1) ** 2 + (-4 - 1) ** 2) / 3.0, rel=1e-15)
 
 
 def test_correction_target_diagonal_closed_form():
@@ -178,4 +187,5 @@ def test_apply_falls_back_to_jacobi_on_non_finite():
     p[L.OFF_B3] = np.nan
     np.testing.assert_array_equal(L.apply(p, F, R, H.diagonal_f64(), th), O.jacobi_apply(H.diagonal_f64(), th, R))
     p[L.OFF_B3] = 0.5
-    np.testing.assert_array_equal(L.apply(p, F, R, H.diagonal_f64(), th), 0.5 * R)
+    np.testing.assert_allclose(L.apply(p, F, R, H.diagonal_f64(), th),
+                               1.5 * O.jacobi_apply(H.diagonal_f64(), th, R, 2.0), rtol=1e-15)
