@@ -61,6 +61,17 @@ def parse():
                     help="largest DIIS window of RMM-DIIS (Alg. 4 input s)")
     ap.add_argument("--layout", default="auto", choices=["auto", "mirrored", "half", "csr"],
                     help="device layout of the SpMM plan")
+    ap.add_argument("--workload", default="hybrid", choices=["hybrid", "learned"],
+                    help="hybrid: the time-to-solution line; learned: train the learned K on a matrix "
+                         "family and compare it with Jacobi on held-out members")
+    ap.add_argument("--lp-n", type=int, default=1_000_000)
+    ap.add_argument("--lp-nnz-per-row", type=float, default=300)
+    ap.add_argument("--lp-train", type=int, default=48)
+    ap.add_argument("--lp-held", type=int, default=16)
+    ap.add_argument("--lp-epochs", type=int, default=10)
+    ap.add_argument("--lp-switch-res", type=float, default=1e-3,
+                    help="learned workload: LOBPCG front to this residual, then RMM-DIIS (the family's "
+                         "near-degenerate shells need a later switch than 1e-2)")
     return ap.parse_args()
 
 
@@ -260,9 +271,147 @@ def workload_config(args, H):
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
+def run_learned(args, ws, rank, local):
+    """The learned-preconditioner workload: H(g) = H0 + g V (n = --lp-n, ~--lp-nnz-per-row nonzeros
+    per full row, block pattern 256, FP32 values; V on H0's pattern, N(0, 0.1^2)), g uniform in
+    [0.5, 1.5].  The K is trained on LOBPCG iterates of the training members (on the GPU, by the
+    library's kernels), then the hybrid solve (FP32 vectors, n_ev, block, tol 1e-6) with the
+    learned K is timed against the same solve with the Jacobi K on each held-out member, from the
+    small-space start.  Every rank runs the whole workload (replicas)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2305_15552_gb300 import binding, learned as LG
+    from gen import ci_matrix, family_perturbation, family_member
+    lib = binding.load()
+    t = time.time()
+    H0 = ci_matrix(args.lp_n, args.lp_nnz_per_row, args.block_pattern, seed=args.seed, storage=args.storage)
+    V = family_perturbation(H0, seed=args.seed + 100)
+    tgen = time.time() - t
+    gs = np.random.default_rng(args.seed).uniform(0.5, 1.5, args.lp_train + args.lp_held)
+    samples, held_samples, held = [], [], []
+    t = time.time()
+    for q, g in enumerate(gs):
+        Hq = family_member(H0, V, g)
+        try:
+            X0 = initial_guess(Hq, args, binding)
+        except binding.EigError as e:   # a start that the small solve could not use: another seed
+            print(f"member {q}: initial guess failed ({e}); retrying with another seed", file=sys.stderr)
+            X0 = initial_guess(Hq, argparse.Namespace(**{**vars(args), "seed": args.seed + 17}), binding)
+        S = binding.Solver(Hq, args.nev, args.nb)
+        if q < args.lp_train:
+            samples += LG.collect_samples(S, X0, iters=(0, 1, 2, 3, 5))
+        else:
+            held_samples += LG.collect_samples(S, X0, iters=(0, 2))
+            held.append((g, X0))
+        S.close()
+    t_samples = time.time() - t
+    p0 = LG.init_params(*LG.feature_stats(samples), seed=0)
+    torch.cuda.synchronize()
+    t = time.time()
+    p, hist = LG.train(samples, p0, epochs=args.lp_epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t
+    loss_lp = LG.mean_loss(held_samples, p)
+    loss_j = float(np.mean([LG.jacobi_loss(s_) for s_ in held_samples]))
+    # throughput of the network kernel (inference on one sample's feature rows), FP32 ALU bound
+    F = held_samples[0]["F"]
+    for _ in range(3):
+        binding.lp_forward(p, F)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    with ClockSampler(local) as clk_mlp:
+        e0.record()
+        for _ in range(reps):
+            binding.lp_forward(p, F)
+        e1.record()
+        torch.cuda.synchronize()
+    mlp_ms = e0.elapsed_time(e1) / reps
+    del samples, held_samples, F
+    torch.cuda.empty_cache()
+    # held-out solves: Jacobi K and learned K
+    base = dict(vec_type=args.vec, tol=args.tol, timing=1, maxiter=500, switch_res=args.lp_switch_res,
+                switch_tau=args.switch_tau, s_max=args.s_max)
+    rows = []
+    launches0 = lib.eig_launch_count()
+    with ClockSampler(local) as clk:
+        for g, X0 in held:
+            Hq = family_member(H0, V, g)
+            S = binding.Solver(Hq, args.nev, args.nb)
+            X0d = torch.tensor(X0, device="cuda")
+            res = {}
+            for name, o in (("jacobi", dict(precond=1, rmm_precond=1)),
+                            ("learned", dict(precond=2, rmm_precond=2, lp_params=p)),
+                            ("learned_front", dict(precond=2, rmm_precond=1, lp_params=p)),
+                            ("fp64_jacobi", dict(precond=1, rmm_precond=1, vec_type="f64"))):
+                oo = {**base, **o}
+                S.solve("hybrid", X0=X0d, **oo)        # warm-up
+                torch.cuda.synchronize()
+                e0.record()
+                rc, st = S.solve("hybrid", X0=X0d, **oo)
+                e1.record()
+                torch.cuda.synchronize()
+                res[name] = dict(ms=e0.elapsed_time(e1), rc=rc, front=st["iterations_front"],
+                                 rmm=st["iterations_rmm"], safety=st["iterations_fallback"],
+                                 spmm=st["spmm_calls"], lp_spmm=st["lp_spmm_calls"],
+                                 k_fallback=st["precond_fallback"], max_relres=st["max_relres"])
+            rows.append(res)
+            S.close()
+    launches = lib.eig_launch_count() - launches0
+    ms_lp = float(np.mean([r["learned"]["ms"] for r in rows]))
+    ms_j = float(np.mean([r["jacobi"]["ms"] for r in rows]))
+    arms = ("jacobi", "learned", "learned_front", "fp64_jacobi")
+    conv = {a: sum(r[a]["rc"] == 0 for r in rows) for a in arms}
+    both = [r for r in rows if all(r[a]["rc"] == 0 for a in arms)]
+    arm_ms = {a: float(np.mean([r[a]["ms"] for r in rows])) for a in arms}
+    both_ms = {a: (float(np.mean([r[a]["ms"] for r in both])) if both else None) for a in arms}
+    ms_lp = reduce_max(ms_lp, ws, "cuda")
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(local)
+    mhz = clk_mlp.summary().get("sm_mhz") or clocks.get("sm_mhz") or 2070.0
+    alu_peak = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
+    flops_row = 2 * (6 * 32 + 32 * 32 + 32) + 20
+    n_rows = args.lp_n * args.nev
+    achieved = n_rows * flops_row / (mlp_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": ms_lp, "unit": "ms", "n_gpus": args.gpus, "steps": len(rows), "warmup": 1,
+        "ms_per_step": ms_lp, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.vec, "data": "synthetic",
+        "config": {"workload": (f"learned preconditioner: H(g) = H0 + g V, n={args.lp_n:,}, ~{args.lp_nnz_per_row:g} "
+                                f"nnz/row, block pattern {args.block_pattern}, {args.storage} values, g in [0.5, 1.5], "
+                                f"{args.lp_train} training / {args.lp_held} held-out members; hybrid LOBPCG "
+                                f"(to residual {args.lp_switch_res:g}) -> RMM-DIIS, n_ev={args.nev}, block {args.nb}, "
+                                f"tol {args.tol:g}, learned K vs Jacobi K; value = mean held-out time-to-solution "
+                                f"with the learned K"),
+                   "n": args.lp_n, "n_ev": args.nev, "block": args.nb, "train": args.lp_train,
+                   "held_out": args.lp_held, "epochs": args.lp_epochs, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (matrix ~1.2 GB), no flush"},
+        "jacobi_ms": ms_j, "speedup_vs_jacobi": ms_j / ms_lp,
+        "mean_ms": arm_ms,
+        "converged": {**conv, "of": len(rows)},
+        "all_converged": {"count": len(both), "mean_ms": both_ms},
+        "held_out_loss": {"learned": loss_lp, "jacobi": loss_j},
+        "per_matrix": rows,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "k_lp_forward (6-32-32-1 MLP, FP32 FMA)", "achieved": achieved,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                     "peak_kind": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+                     "flops_per_row": flops_row, "rows_per_launch": n_rows, "avg_launch_ms": mlp_ms},
+        "training": {"samples_s": t_samples, "train_s": t_train, "loss_first_epoch": hist[0],
+                     "loss_last_epoch": hist[-1]},
+        "clocks": clocks,
+        "host": {"machine": platform.machine(), "cpus": os.cpu_count(), "gen_s": tgen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
+    if args.workload == "learned" and args.impl == "ours":
+        run_learned(args, ws, rank, local)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
         barrier(ws)

@@ -50,6 +50,12 @@ __global__ void k_pad_columns(const double* __restrict__ src, int ks, double* __
   }
 }
 
+// y += a x over count entries
+__global__ void k_add_scaled(const double* __restrict__ x, double a, double* __restrict__ y, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
 eig_status pad_columns(const double* src, int ks, double* dst, int kd, int64_t n, cudaStream_t st) {
   k_pad_columns<<<num_sms() * 8, 256, 0, st>>>(src, ks, dst, kd, n);
   EIG_LAUNCH_CHECK("k_pad_columns");
@@ -246,12 +252,9 @@ __global__ void k_pair_gram(const double* __restrict__ X, int m, int ld, int64_t
 
 // Two columns of X (n x ld, FP64, first m used) that are collinear (|cos| >= 0.9) with Ritz values
 // equal to 1e-6 relative: RMM-DIIS does not orthogonalise its vectors (Sec. 3.3).
-eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::vector<double>& theta,
-                           bool* duplicate) {
-  *duplicate = false;
-  if (m < 2) return EIG_OK;
+// Symmetric Gram matrix hg (ld x ld, host) of the first m columns of X (n x ld, FP64).
+static eig_status column_gram(Ctx& c, const double* X, int m, int ld, std::vector<double>* hg) {
   const int npairs = m * (m + 1) / 2;
-  if (npairs > 256) return EIG_OK;  // n_ev > 22: no check
   const int grid = num_sms() * 4;
   DevBuf gbuf;
   EIG_TRY(gbuf.reserve((size_t)grid * npairs * 8 + (size_t)npairs * 8));
@@ -260,11 +263,22 @@ eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::ve
   k_pair_gram<<<grid, 256, 0, c.st>>>(X, m, ld, c.h->n, part);
   EIG_LAUNCH_CHECK("k_pair_gram");
   EIG_TRY(reduce_partials(part, grid, npairs, Gp, c.st));
-  std::vector<double> hp(npairs), hg((size_t)ld * ld, 0.0);
+  std::vector<double> hp(npairs);
+  hg->assign((size_t)ld * ld, 0.0);
   EIG_CUDA_TRY(cudaMemcpyAsync(hp.data(), Gp, npairs * 8, cudaMemcpyDeviceToHost, c.st));
   EIG_TRY(c.sync());
   for (int i = 0, q = 0; i < m; ++i)
-    for (int j = i; j < m; ++j, ++q) hg[(size_t)i * ld + j] = hg[(size_t)j * ld + i] = hp[q];
+    for (int j = i; j < m; ++j, ++q) (*hg)[(size_t)i * ld + j] = (*hg)[(size_t)j * ld + i] = hp[q];
+  return EIG_OK;
+}
+
+eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::vector<double>& theta,
+                           bool* duplicate) {
+  *duplicate = false;
+  if (m < 2) return EIG_OK;
+  if (m * (m + 1) / 2 > 256) return EIG_OK;  // n_ev > 22: no check
+  std::vector<double> hg;
+  EIG_TRY(column_gram(c, X, m, ld, &hg));
   for (int i = 0; i < m; ++i)
     for (int j = i + 1; j < m; ++j) {
       const double gi = hg[(size_t)i * ld + i], gj = hg[(size_t)j * ld + j];
@@ -273,6 +287,42 @@ eig_status find_duplicates(Ctx& c, const double* X, int m, int ld, const std::ve
       if (cosv >= 0.9 && std::fabs(theta[i] - theta[j]) <= 1e-6 * scale) *duplicate = true;
     }
   return EIG_OK;
+}
+
+// Columns of X (n x ld, first m) to keep as a start block: in order, a column is dropped when
+// |cos| with a kept one is >= cos_max (RMM-DIIS can leave several on one eigenvector).
+static eig_status independent_columns(Ctx& c, const double* X, int m, int ld, double cos_max, std::vector<int>* keep) {
+  keep->clear();
+  if (m * (m + 1) / 2 > 256) {
+    for (int j = 0; j < m; ++j) keep->push_back(j);
+    return EIG_OK;
+  }
+  std::vector<double> hg;
+  EIG_TRY(column_gram(c, X, m, ld, &hg));
+  for (int j = 0; j < m; ++j) {
+    const double gj = hg[(size_t)j * ld + j];
+    bool ok = gj > 0.0;
+    for (int i : *keep) {
+      const double gi = hg[(size_t)i * ld + i];
+      if (std::fabs(hg[(size_t)i * ld + j]) >= cos_max * std::sqrt(gi * gj)) ok = false;
+    }
+    if (ok) keep->push_back(j);
+  }
+  return EIG_OK;
+}
+
+struct ColIdx {
+  int c[32];
+};
+
+// dst (n x kd) column q <- src (n x ks) column idx.c[q]
+__global__ void k_gather_columns(const double* __restrict__ src, int ks, ColIdx idx, int kd, double* __restrict__ dst,
+                                 int64_t n) {
+  const int64_t total = n * kd;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / kd;
+    dst[i] = src[r * ks + idx.c[i % kd]];
+  }
 }
 
 // Also flags duplicates: two returned vectors that are collinear (|cos| >= 0.9) with Ritz values
@@ -370,10 +420,10 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   } else {
     EIG_TRY(pad_columns(X0, x0_cols, X0p, nb, n, c.st));  // the first nb columns
   }
-  EIG_TRY(convert(X0p, EIG_F64, X, vt, n * nb, c.st));
   // initial Rayleigh-Ritz on X0 (Alg. 2 line 1)
-  EIG_TRY(c.spmm(X, HX, nb, vt, nb));
-  {
+  for (int attempt = 0;; ++attempt) {
+    EIG_TRY(convert(X0p, EIG_F64, X, vt, n * nb, c.st));
+    EIG_TRY(c.spmm(X, HX, nb, vt, nb));
     BlockList bl;
     bl.n = 2;
     bl.p[0] = X;
@@ -388,7 +438,8 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
     mp.idx[0][0] = 1;
     k_assemble<<<1, 256, 0, c.st>>>(Gp, mp, 1, nb, A);
     EIG_LAUNCH_CHECK("k_assemble");
-    EIG_TRY(small_rr(A, G, nb, nb, piv_tol, theta, C, nullptr, rrwork, info, c.st));
+    // a start block closer to rank deficiency than this is perturbed below rather than used
+    EIG_TRY(small_rr(A, G, nb, nb, std::max(piv_tol, 1e-10), theta, C, nullptr, rrwork, info, c.st));
     BlockList in;
     in.n = 1;
     in.p[0] = X;
@@ -405,7 +456,15 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
     if (lp_on) EIG_TRY(lp_precondition(c, W, HW, nb, nb, vt, theta, rsq, nullptr, nb, W, nonfin));
     EIG_CUDA_TRY(cudaMemcpyAsync(hstat, stat, (2 * nb + 8) * 8, cudaMemcpyDeviceToHost, c.st));
     EIG_TRY(c.sync());
-    if (*reinterpret_cast<int*>(hstat + 2 * nb) != SMALL_OK) return EIG_EBREAKDOWN;
+    if (*reinterpret_cast<int*>(hstat + 2 * nb) == SMALL_OK) break;
+    if (attempt == 2) return EIG_EBREAKDOWN;
+    // the start block is numerically rank deficient (two guesses nearly parallel, as RMM-DIIS
+    // can leave them): mix in a seeded random block of 1% of a unit column's norm and retry
+    DevBuf rnd;
+    EIG_TRY(rnd.reserve((size_t)n * nb * 8));
+    EIG_TRY(fill_random(rnd.as<double>(), n * nb, c.o.seed + 1001 + attempt, c.st));
+    k_add_scaled<<<num_sms() * 8, 256, 0, c.st>>>(rnd.as<double>(), 1e-2 / std::sqrt((double)n), X0p, n * nb);
+    EIG_LAUNCH_CHECK("k_add_scaled");
   }
   std::vector<double> th(nb), rel(nb);
   auto read_status = [&]() {
@@ -1052,9 +1111,18 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
       DevBuf Xf2, X0f;
       EIG_TRY(Xf2.reserve((size_t)n * nb * 8));
       EIG_TRY(X0f.reserve((size_t)n * nev * 8));
-      EIG_CUDA_TRY(cudaMemcpyAsync(X0f.p, h->Xres.p, (size_t)n * nev * 8, cudaMemcpyDeviceToDevice, c.st));
-      const eig_status fr = run_lobpcg(c, X0f.as<double>(), nev, c.o.maxiter, StopFn(), &fit, &freason, &fc,
-                                       Xf2.as<double>(), &theta);
+      // start from the RMM-DIIS vectors without the ones that repeat another (LOBPCG fills the
+      // block up with seeded random columns)
+      std::vector<int> keep;
+      EIG_TRY(independent_columns(c, h->Xres.as<double>(), nev, nev, 0.5, &keep));
+      if (keep.empty()) keep.push_back(0);
+      ColIdx ci;
+      for (int q = 0; q < 32; ++q) ci.c[q] = q < (int)keep.size() ? keep[q] : 0;
+      k_gather_columns<<<num_sms() * 8, 256, 0, c.st>>>(h->Xres.as<double>(), nev, ci, (int)keep.size(),
+                                                        X0f.as<double>(), n);
+      EIG_LAUNCH_CHECK("k_gather_columns");
+      const eig_status fr = run_lobpcg(c, X0f.as<double>(), (int)keep.size(), c.o.maxiter, StopFn(), &fit,
+                                       &freason, &fc, Xf2.as<double>(), &theta);
       c.o.vec_type = vt_saved;
       c.o.precond = pre_saved;
       EIG_TRY(fr);
