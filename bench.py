@@ -5,7 +5,7 @@ seeded 256 x 256 block pattern, half-stored (~4e8 stored nonzeros), FP32 values;
 n_ev = 8 eigenpairs, block n_b = 16, LOBPCG front switched to batched RMM-DIIS by the tau rule
 of Eq. (switchtau), relative residual 1e-6.  The initial guess is the zero-padded lowest
 eigenvectors of the leading n/10 principal block (the smaller-model-space start of Sec. 3.1),
-computed beforehand on the GPU and excluded from the timing, as in the paper.
+computed beforehand on the GPU (FP64 LOBPCG to 1e-8) and excluded from the timing, as in the paper.
 
 A step is one complete solve (eig_solve) with H resident in HBM.  `e2e` repeats the metric
 through the C ABI from host buffers: eig_create (H copied in and planned), eig_solve with a
@@ -61,7 +61,9 @@ def parse():
                     help="largest DIIS window of RMM-DIIS (Alg. 4 input s)")
     ap.add_argument("--layout", default="auto", choices=["auto", "mirrored", "half", "csr"],
                     help="device layout of the SpMM plan")
-    ap.add_argument("--workload", default="hybrid", choices=["hybrid", "learned"],
+    ap.add_argument("--batch-count", type=int, default=32)
+    ap.add_argument("--batch-threads", type=int, default=16)
+    ap.add_argument("--workload", default="hybrid", choices=["hybrid", "learned", "batch"],
                     help="hybrid: the time-to-solution line; learned: train the learned K on a matrix "
                          "family and compare it with Jacobi on held-out members")
     ap.add_argument("--lp-n", type=int, default=1_000_000)
@@ -173,12 +175,13 @@ def make_problem(args):
 
 
 def initial_guess(H, args, binding):
-    """Zero-padded lowest eigenvectors of the leading n/10 principal block, solved on the GPU."""
+    """Zero-padded lowest n_b eigenvectors of the leading n/10 principal block (the smaller model
+    space of Sec. 3.1), solved on the GPU by LOBPCG with FP64 vectors to relative residual 1e-8."""
     from gen import principal_submatrix, pad_rows
     n0 = max(args.nb * 8, H.n // 10)
     H0 = principal_submatrix(H, n0)
     S0 = binding.Solver(H0, args.nb, args.nb)
-    rc, st = S0.solve("hybrid", vec_type=args.vec, tol=1e-4, seed=args.seed)
+    rc, st = S0.solve("lobpcg", vec_type="f64", tol=1e-8, maxiter=1000, seed=args.seed)
     _, X0, _ = S0.ritz()
     S0.close()
     return pad_rows(X0, H.n)
@@ -364,7 +367,7 @@ def run_learned(args, ws, rank, local):
     both = [r for r in rows if all(r[a]["rc"] == 0 for a in arms)]
     arm_ms = {a: float(np.mean([r[a]["ms"] for r in rows])) for a in arms}
     both_ms = {a: (float(np.mean([r[a]["ms"] for r in both])) if both else None) for a in arms}
-    ms_lp = reduce_max(ms_lp, ws, "cuda")
+    ms_val = reduce_max(arm_ms["learned_front"], ws, "cuda")
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(local)
     mhz = clk_mlp.summary().get("sm_mhz") or clocks.get("sm_mhz") or 2070.0
@@ -373,19 +376,22 @@ def run_learned(args, ws, rank, local):
     n_rows = args.lp_n * args.nev
     achieved = n_rows * flops_row / (mlp_ms * 1e-3) / 1e12
     line = {
-        "metric": METRIC, "value": ms_lp, "unit": "ms", "n_gpus": args.gpus, "steps": len(rows), "warmup": 1,
-        "ms_per_step": ms_lp, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": ms_val, "unit": "ms", "n_gpus": args.gpus, "steps": len(rows), "warmup": 1,
+        "ms_per_step": ms_val, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": args.vec, "data": "synthetic",
         "config": {"workload": (f"learned preconditioner: H(g) = H0 + g V, n={args.lp_n:,}, ~{args.lp_nnz_per_row:g} "
                                 f"nnz/row, block pattern {args.block_pattern}, {args.storage} values, g in [0.5, 1.5], "
                                 f"{args.lp_train} training / {args.lp_held} held-out members; hybrid LOBPCG "
                                 f"(to residual {args.lp_switch_res:g}) -> RMM-DIIS, n_ev={args.nev}, block {args.nb}, "
                                 f"tol {args.tol:g}, learned K vs Jacobi K; value = mean held-out time-to-solution "
-                                f"with the learned K"),
+                                f"with the learned K in the LOBPCG front and Jacobi in RMM-DIIS (every arm in "
+                                f"mean_ms: jacobi, learned in both phases, learned_front, fp64_jacobi = FP64 "
+                                f"vectors with Jacobi)"),
                    "n": args.lp_n, "n_ev": args.nev, "block": args.nb, "train": args.lp_train,
                    "held_out": args.lp_held, "epochs": args.lp_epochs, "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (matrix ~1.2 GB), no flush"},
-        "jacobi_ms": ms_j, "speedup_vs_jacobi": ms_j / ms_lp,
+        "jacobi_ms": ms_j, "speedup_vs_jacobi": ms_j / arm_ms["learned_front"],
+        "speedup_vs_fp64_jacobi": arm_ms["fp64_jacobi"] / arm_ms["learned_front"],
         "mean_ms": arm_ms,
         "converged": {**conv, "of": len(rows)},
         "all_converged": {"count": len(both), "mean_ms": both_ms},
@@ -406,9 +412,104 @@ def run_learned(args, ws, rank, local):
     barrier(ws)
 
 
+def run_batch(args, ws, rank, local):
+    """Batched uneven instances: --batch-count matrices with n log-uniform in [2e4, 5e5] and 50-300
+    nonzeros per full row (same generator, block pattern 256, FP32 values, seed = base + index),
+    n_ev = 5, block 8; each from its small-space start (computed beforehand, not timed).  Arms,
+    each timed on the device over the whole batch: one instance after another on one stream;
+    eig_solve_batch with worker streams; the same with each instance's SpMM plan shape chosen by
+    eig_autotune_spmm (tuning not timed).  Every rank runs the whole batch (replicas)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2305_15552_gb300 import binding
+    from gen import ci_matrix
+    lib = binding.load()
+    nev, nb = 5, 8
+    a2 = argparse.Namespace(**{**vars(args), "nev": nev, "nb": nb})
+    rng = np.random.default_rng(args.seed)
+    ns = np.round(np.exp(rng.uniform(np.log(2e4), np.log(5e5), args.batch_count))).astype(int)
+    nz = rng.uniform(50, 300, args.batch_count)
+    t = time.time()
+    Hs = [ci_matrix(int(n), float(z), args.block_pattern, seed=args.seed + 1000 + i, storage="f32")
+          for i, (n, z) in enumerate(zip(ns, nz))]
+    tgen = time.time() - t
+    X0s = [torch.tensor(initial_guess(H, a2, binding), device="cuda") for H in Hs]
+    opts = dict(vec_type="f32", tol=args.tol, maxiter=500, switch_res=args.lp_switch_res, switch_tau=0.0,
+                s_max=args.s_max)
+    tuned = [binding.autotune_spmm(H, nb, "f32", reps=3)[0] for H in Hs]
+    S_def = [binding.Solver(H, nev, nb) for H in Hs]
+    S_tun = [binding.Solver(H, nev, nb, layout=tb["layout"], row_block=tb["row_block"], col_block=tb["col_block"])
+             for H, tb in zip(Hs, tuned)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+
+    def seq():
+        out = []
+        for S, X0 in zip(S_def, X0s):
+            out.append(S.solve("hybrid", X0=X0, **opts))
+        return out
+
+    def timed(fn):
+        fn()                                  # warm-up
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    launches0 = lib.eig_launch_count()
+    with ClockSampler(local) as clk:
+        ms_seq, out_seq = timed(seq)
+        ms_bat, out_bat = timed(lambda: binding.solve_batch(S_def, "hybrid", X0s=X0s, opts=opts,
+                                                            threads=args.batch_threads))
+        ms_tun, out_tun = timed(lambda: binding.solve_batch(S_tun, "hybrid", X0s=X0s, opts=opts,
+                                                            threads=args.batch_threads))
+    launches = lib.eig_launch_count() - launches0
+    same = all(np.array_equal(a.ritz()[0], b.ritz()[0]) for a, b in zip(S_def, S_tun))
+    conv_seq = sum(rc == 0 for rc, _ in out_seq)
+    conv_bat = sum(s_ == 0 for s_ in out_bat[1])
+    conv_tun = sum(s_ == 0 for s_ in out_tun[1])
+    max_rel = max(float(np.max(S.ritz()[2])) for S in S_tun)
+    for S in S_def + S_tun:
+        S.close()
+    ms_tun = reduce_max(ms_tun, ws, "cuda")
+    layouts = {}
+    for tb in tuned:
+        k = f"{tb['layout']} {tb['row_block']}/{tb['col_block']}"
+        layouts[k] = layouts.get(k, 0) + 1
+    line = {
+        "metric": METRIC, "value": ms_tun, "unit": "ms", "n_gpus": args.gpus, "steps": 1, "warmup": 1,
+        "ms_per_step": ms_tun, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": (f"batched uneven instances: {args.batch_count} matrices, n log-uniform in "
+                                f"[20,000, 500,000] (total {int(ns.sum()):,} rows), 50-300 nnz/row, block pattern "
+                                f"{args.block_pattern}, FP32 values/vectors, n_ev={nev}, block {nb}, hybrid LOBPCG (to "
+                                f"residual {args.lp_switch_res:g}) -> RMM-DIIS to {args.tol:g}; value = time to "
+                                f"solve the whole batch with eig_solve_batch ({args.batch_threads} streams) and "
+                                f"autotuned plan shapes"),
+                   "count": args.batch_count, "rows_total": int(ns.sum()), "n_ev": nev, "block": nb,
+                   "threads": args.batch_threads, "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs mostly smaller than L2 individually, ~6 GB in total; no flush"},
+        "sequential_ms": ms_seq, "batched_ms": ms_bat, "batched_tuned_ms": ms_tun,
+        "speedup_vs_sequential": ms_seq / ms_tun, "instances_per_s": args.batch_count / (ms_tun * 1e-3),
+        "converged": {"sequential": conv_seq, "batched": conv_bat, "batched_tuned": conv_tun,
+                      "of": args.batch_count},
+        "tuned_eigenvalues_equal_default": bool(same), "max_relres": max_rel, "tuned_shapes": layouts,
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "host": {"machine": platform.machine(), "cpus": os.cpu_count(), "gen_s": tgen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
+    if args.workload == "batch" and args.impl == "ours":
+        run_batch(args, ws, rank, local)
+        return
     if args.workload == "learned" and args.impl == "ours":
         run_learned(args, ws, rank, local)
         return

@@ -311,6 +311,45 @@ EIG_API eig_status eig_solve(void* handle, eig_method method, const eig_opts* op
 EIG_API eig_status eig_ritz(void* handle, double* theta, double* X, double* relres, int on_device);
 
 /* ------------------------------------------------------------------------------------ *
+ * Batches of independent instances and the SpMM plan autotuner                         *
+ * ------------------------------------------------------------------------------------ *
+ * Secs. 1 and 4.3 argue for concurrency at the level of eigenpairs: independent small pieces of
+ * work only fill a wide machine when they run side by side.  Many small matrices (each far too
+ * small to fill 152 SMs, each synchronising with the host once per iteration) are solved
+ * together by eig_solve_batch. */
+
+/* eig_create_ex with the SpMM plan's row block R and column block C given (0 = 256 / 64; see
+ * eig_spmm_plan_create_ex for the constraints), e.g. the shape eig_autotune_spmm chose. */
+EIG_API eig_status eig_create_ex2(const eig_csr_upper* H, int n_ev, int block, int layout, int row_block,
+                                  int col_block, void** handle);
+
+/* Solves count independent instances (handles from eig_create*) with one method.  opts: NULL =
+ * defaults for all; otherwise opts[i] for instance i when per_instance_opts != 0, else opts[0]
+ * for all (an X0 given there is then shared).  `threads` host threads (0 = min(count, 16)) take
+ * instances in index order; each owns a non-blocking stream, used by every instance whose
+ * opts.stream is NULL, so the instances' kernels overlap on the GPU.  The results are those of
+ * eig_solve on each handle alone (every kernel is deterministic).  status[i], stats[i] (may be
+ * NULL) receive each instance's eig_solve result.  Returns EIG_OK, or the first status other
+ * than EIG_OK / EIG_ENOT_CONVERGED / EIG_EDUPLICATE.  A handle must not appear twice. */
+EIG_API eig_status eig_solve_batch(void* const* handles, int count, eig_method method, const eig_opts* opts,
+                                   int per_instance_opts, int threads, eig_status* status, eig_stats* stats);
+
+typedef struct {
+  int layout;       /* eig_layout */
+  int row_block;    /* R */
+  int col_block;    /* C */
+  double ms;        /* mean time of one SpMM with the tuning block */
+} eig_tune_result;
+
+/* Times Y = H X (nb columns of vec_type, reps repetitions after two warm-ups) for each
+ * candidate plan shape -- mirrored (256/64), half-stored tiles (256/64, 128/64, 512/128), CSR
+ * (256/64, 128/32, 512/64) -- and returns the fastest in *best; all[] (room for 8, may be NULL)
+ * and *n_all receive every shape that could be built.  H on host or device (copied once).
+ * Synchronises stream.  EIG_EUNSUPPORTED when no shape could be built. */
+EIG_API eig_status eig_autotune_spmm(const eig_csr_upper* H, int nb, eig_dtype vec_type, int reps,
+                                     eig_tune_result* best, eig_tune_result* all, int* n_all, void* stream);
+
+/* ------------------------------------------------------------------------------------ *
  * Learned per-row preconditioner (a replacement for K of Eq. (wblock))                 *
  * ------------------------------------------------------------------------------------ *
  * The paper leaves K open: it only has to approximate H (Sec. 2.3), and Secs. 5-6 name a

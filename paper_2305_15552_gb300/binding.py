@@ -91,6 +91,12 @@ _SIGS = {
     "eig_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Opts), C.POINTER(Stats)]),
     "eig_ritz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "eig_lp_param_count": (C.c_int, []),
+    "eig_create_ex2": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                 C.POINTER(C.c_void_p)]),
+    "eig_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                  C.c_void_p]),
+    "eig_autotune_spmm": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_int), C.c_void_p]),
     "eig_lp_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "eig_lp_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double,
@@ -311,17 +317,59 @@ def rmm_diis(B, slots, active):
 # ---------------------------------------------------------------------------------------
 # solver handle
 # ---------------------------------------------------------------------------------------
+def _make_opts(lib, X0, opts, n_ev, stream=True):
+    """eig_opts from keyword options (vec_type as 'f32'/'f64', front as a method name, lp_params a
+    parameter vector, X0 numpy (host) or torch (device) FP64 n x k); returns (opts, arrays to keep
+    alive while the call runs, trace buffer or None)."""
+    import numpy as np
+    o = Opts()
+    lib.eig_default_opts(C.byref(o))
+    keeps = []
+    for k, v in opts.items():
+        if k == "lp_params":
+            lp = np.ascontiguousarray(v, dtype=np.float32)
+            assert lp.shape == (N_LP_PARAMS,), lp.shape
+            o.lp_params = lp.ctypes.data_as(C.c_void_p).value
+            keeps.append(lp)
+            continue
+        if k == "vec_type":
+            v = STORAGE[v] if isinstance(v, str) else v
+        if k == "front":
+            v = METHODS[v] if isinstance(v, str) else v
+        setattr(o, k, v)
+    if X0 is not None:
+        if hasattr(X0, "data_ptr"):
+            assert X0.dtype.is_floating_point and X0.element_size() == 8 and X0.is_contiguous()
+            o.X0 = X0.data_ptr()
+            o.x0_on_device = 1
+            keep = X0
+        else:
+            keep = np.ascontiguousarray(X0, dtype=np.float64)
+            o.X0 = keep.ctypes.data_as(C.c_void_p).value
+            o.x0_on_device = 0
+        keeps.append(keep)
+        o.x0_cols = int(keep.shape[1])
+    if stream and not o.stream:
+        o.stream = stream_ptr()
+    tr = None
+    if opts.get("trace_cap", 0):
+        tr = np.zeros((int(opts["trace_cap"]), 2 + 2 * n_ev))
+        o.trace = tr.ctypes.data_as(C.c_void_p).value
+        keeps.append(tr)
+    return o, keeps, tr
+
+
 class Solver:
     """eig_create / eig_solve / eig_ritz / eig_destroy."""
 
-    def __init__(self, H, n_ev, block, layout="auto"):
+    def __init__(self, H, n_ev, block, layout="auto", row_block=0, col_block=0):
         import numpy as np
         self._lib = lib = load()
         rp, cl, vl = (np.ascontiguousarray(H.rowptr), np.ascontiguousarray(H.col), np.ascontiguousarray(H.val))
         st = csr_struct(rp, cl, vl, H.storage, H.n, False)
         h = C.c_void_p()
-        check(lib.eig_create_ex(C.byref(st), int(n_ev), int(block), layout_code(layout), C.byref(h)),
-              "eig_create_ex")
+        check(lib.eig_create_ex2(C.byref(st), int(n_ev), int(block), layout_code(layout), int(row_block),
+                                 int(col_block), C.byref(h)), "eig_create_ex2")
         self._h = h
         self.n, self.n_ev = H.n, n_ev
 
@@ -336,42 +384,11 @@ class Solver:
         n x k array.  Keyword options map to eig_opts fields (vec_type as 'f32'/'f64',
         front as a method name)."""
         import numpy as np
-        o = Opts()
-        self._lib.eig_default_opts(C.byref(o))
-        keep = None
-        keep_lp = None
-        for k, v in opts.items():
-            if k == "lp_params":
-                keep_lp = np.ascontiguousarray(v, dtype=np.float32)
-                assert keep_lp.shape == (N_LP_PARAMS,), keep_lp.shape
-                o.lp_params = keep_lp.ctypes.data_as(C.c_void_p).value
-                continue
-            if k == "vec_type":
-                v = STORAGE[v] if isinstance(v, str) else v
-            if k == "front":
-                v = METHODS[v] if isinstance(v, str) else v
-            setattr(o, k, v)
-        if X0 is not None:
-            if hasattr(X0, "data_ptr"):
-                assert X0.dtype.is_floating_point and X0.element_size() == 8 and X0.is_contiguous()
-                o.X0 = X0.data_ptr()
-                o.x0_on_device = 1
-                keep = X0
-            else:
-                keep = np.ascontiguousarray(X0, dtype=np.float64)
-                o.X0 = keep.ctypes.data_as(C.c_void_p).value
-                o.x0_on_device = 0
-            o.x0_cols = int(keep.shape[1])
-        if not o.stream:
-            o.stream = stream_ptr()
-        tr = None
-        if opts.get("trace_cap", 0):
-            tr = np.zeros((int(opts["trace_cap"]), 2 + 2 * self.n_ev))
-            o.trace = tr.ctypes.data_as(C.c_void_p).value
+        o, keeps, tr = _make_opts(self._lib, X0, opts, self.n_ev)
         stats = Stats()
         rc = self._lib.eig_solve(self._h, METHODS[method] if isinstance(method, str) else int(method), C.byref(o),
                                  C.byref(stats))
-        del keep, keep_lp
+        del keeps
         if rc not in (EIG_OK, EIG_ENOT_CONVERGED, EIG_EDUPLICATE):
             raise EigError(rc, "eig_solve")
         st = {k: getattr(stats, k) for k, _ in Stats._fields_}
@@ -474,3 +491,58 @@ def lp_adam(params_dev, grad, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """eig_lp_adam: one Adam step on params_dev (device FP32, in place)."""
     check(load().eig_lp_adam(params_dev.data_ptr(), grad.data_ptr(), m1.data_ptr(), m2.data_ptr(), int(t),
                              float(lr), float(beta1), float(beta2), float(eps), stream_ptr()), "eig_lp_adam")
+
+
+# ---------------------------------------------------------------------------------------
+# batches of instances, SpMM plan autotuner
+# ---------------------------------------------------------------------------------------
+class TuneResult(C.Structure):
+    _fields_ = [("layout", C.c_int), ("row_block", C.c_int), ("col_block", C.c_int), ("ms", C.c_double)]
+
+
+LAYOUT_NAMES = {v: k for k, v in LAYOUTS.items()}
+
+
+def solve_batch(solvers, method="hybrid", X0s=None, opts=None, threads=0):
+    """eig_solve_batch over Solver objects; X0s: list (per instance) or None; opts: one dict for
+    all or a list of dicts.  Instances without a stream run on the batch's worker streams.
+    Returns (status of the batch, [status], [stats dict])."""
+    lib = load()
+    cnt = len(solvers)
+    per = isinstance(opts, (list, tuple)) or X0s is not None
+    arr = (Opts * max(cnt, 1))()
+    keeps = []
+    for i in range(cnt if per else 1):
+        od = dict(opts[i] if isinstance(opts, (list, tuple)) else (opts or {}))
+        o, kp, _ = _make_opts(lib, None if X0s is None else X0s[i], od, solvers[i].n_ev, stream=False)
+        arr[i] = o
+        keeps.append(kp)
+    hs = (C.c_void_p * max(cnt, 1))(*[s_._h for s_ in solvers])
+    st = (C.c_int * max(cnt, 1))()
+    stats = (Stats * max(cnt, 1))()
+    import torch
+    torch.cuda.synchronize()
+    rc = lib.eig_solve_batch(hs, cnt, METHODS[method] if isinstance(method, str) else int(method), arr,
+                             1 if per else 0, int(threads), st, stats)
+    del keeps
+    out = [{k: getattr(stats[i], k) for k, _ in Stats._fields_} for i in range(cnt)]
+    return rc, [int(st[i]) for i in range(cnt)], out
+
+
+def autotune_spmm(H, nb, vec_type="f32", reps=5):
+    """eig_autotune_spmm: the fastest SpMM plan shape for H with an nb-column block.  Returns
+    (best, all) as dicts {layout, row_block, col_block, ms}."""
+    import numpy as np
+    lib = load()
+    rp, cl, vl = (np.ascontiguousarray(H.rowptr), np.ascontiguousarray(H.col), np.ascontiguousarray(H.val))
+    st = csr_struct(rp, cl, vl, H.storage, H.n, False)
+    best = TuneResult()
+    allr = (TuneResult * 8)()
+    na = C.c_int(0)
+    check(lib.eig_autotune_spmm(C.byref(st), int(nb), STORAGE[vec_type] if isinstance(vec_type, str) else vec_type,
+                                int(reps), C.byref(best), allr, C.byref(na), stream_ptr()), "eig_autotune_spmm")
+
+    def d(r):
+        return {"layout": LAYOUT_NAMES.get(r.layout, r.layout), "row_block": r.row_block, "col_block": r.col_block,
+                "ms": r.ms}
+    return d(best), [d(allr[i]) for i in range(na.value)]

@@ -1,0 +1,166 @@
+// Many independent instances: concurrent solves of a batch of handles, and an autotuner of the
+// SpMM plan shape.
+//
+// The paper's point about eigenpair-level concurrency (Secs. 1, 4.3) is that small independent
+// pieces of work only fill a wide machine when they run side by side.  A batch of uneven
+// matrices is the extreme case: one instance of 2e4 rows leaves most of the 152 SMs idle, and a
+// solve synchronises with the host once per iteration.  eig_solve_batch therefore runs the
+// instances from a pool of host threads, each with its own non-blocking stream, so that the
+// kernels and host round trips of different instances overlap.
+#include <algorithm>
+#include <atomic>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "solver.cuh"
+#include "spmm.cuh"
+
+namespace eig {
+namespace {
+
+template <typename T>
+__global__ void k_tune_fill(T* X, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    // deterministic values in [-1, 1)
+    uint32_t h = (uint32_t)(i * 2654435761u) ^ 0x9E3779B9u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    X[i] = (T)((double)(h & 0xFFFFFF) / 8388608.0 - 1.0);
+  }
+}
+
+bool is_hard_error(eig_status s) {
+  return s != EIG_OK && s != EIG_ENOT_CONVERGED && s != EIG_EDUPLICATE;
+}
+
+}  // namespace
+}  // namespace eig
+
+using namespace eig;
+
+extern "C" {
+
+eig_status eig_solve_batch(void* const* handles, int count, eig_method method, const eig_opts* opts,
+                           int per_instance_opts, int threads, eig_status* status, eig_stats* stats) {
+  if (count < 0 || (count > 0 && !handles)) return EIG_EINVAL;
+  if (per_instance_opts && !opts) return EIG_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!handles[i]) return EIG_EINVAL;
+  if (count == 0) return EIG_OK;
+  int dev = 0;
+  EIG_CUDA_TRY(cudaGetDevice(&dev));
+  const int nt = std::max(1, std::min(count, threads > 0 ? threads : 16));
+  std::vector<eig_status> st(count, EIG_OK);
+  std::vector<eig_stats> ss(count);
+  std::atomic<int> next(0);
+  std::atomic<int> setup_error(0);
+  auto worker = [&]() {
+    if (cudaSetDevice(dev) != cudaSuccess) { setup_error = 1; return; }
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { setup_error = 1; return; }
+    for (int i = next++; i < count; i = next++) {
+      eig_opts o;
+      if (!opts) eig_default_opts(&o);
+      else o = per_instance_opts ? opts[i] : opts[0];
+      if (!o.stream) o.stream = s;
+      st[i] = eig_solve(handles[i], method, &o, &ss[i]);
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(nt);
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  if (setup_error) return EIG_ECUDA;
+  eig_status first = EIG_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = st[i];
+    if (stats) stats[i] = ss[i];
+    if (first == EIG_OK && is_hard_error(st[i])) first = st[i];
+  }
+  return first;
+}
+
+eig_status eig_autotune_spmm(const eig_csr_upper* H, int nb, eig_dtype vec_type, int reps, eig_tune_result* best,
+                             eig_tune_result* all, int* n_all, void* stream) {
+  if (!H || !best || nb < 1 || nb > 32 || (nb & (nb - 1)) || reps < 1) return EIG_EINVAL;
+  if (vec_type != EIG_F32 && vec_type != EIG_F64) return EIG_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  const int64_t n = H->n, nnz = H->nnz;
+  if (n < 1 || nnz < 0) return EIG_EINVAL;
+  const size_t vb = H->val_type == EIG_F64 ? 8 : (H->val_type == EIG_F32 ? 4 : 2);
+  // one device copy of H shared by every candidate plan
+  DevBuf rp, cl, vl;
+  eig_csr_upper Hd = *H;
+  if (!H->on_device) {
+    EIG_TRY(rp.reserve((size_t)(n + 1) * 8));
+    EIG_TRY(cl.reserve(std::max<int64_t>(nnz, 1) * 4));
+    EIG_TRY(vl.reserve(std::max<int64_t>(nnz, 1) * vb));
+    EIG_CUDA_TRY(cudaMemcpyAsync(rp.p, H->rowptr, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (nnz) {
+      EIG_CUDA_TRY(cudaMemcpyAsync(cl.p, H->col, (size_t)nnz * 4, cudaMemcpyHostToDevice, st));
+      EIG_CUDA_TRY(cudaMemcpyAsync(vl.p, H->val, (size_t)nnz * vb, cudaMemcpyHostToDevice, st));
+    }
+    Hd.rowptr = rp.as<int64_t>();
+    Hd.col = cl.as<int32_t>();
+    Hd.val = vl.p;
+    Hd.on_device = 1;
+  }
+  const size_t es = vec_type == EIG_F64 ? 8 : 4;
+  DevBuf X, Y;
+  EIG_TRY(X.reserve((size_t)n * nb * es));
+  EIG_TRY(Y.reserve((size_t)n * nb * es));
+  const int fg = num_sms() * 4;
+  if (vec_type == EIG_F64) k_tune_fill<double><<<fg, 256, 0, st>>>(X.as<double>(), n * nb);
+  else k_tune_fill<float><<<fg, 256, 0, st>>>(X.as<float>(), n * nb);
+  EIG_LAUNCH_CHECK("k_tune_fill");
+  static const int cand[][3] = {{EIG_LAYOUT_MIRRORED, 256, 64}, {EIG_LAYOUT_HALF, 256, 64},
+                                {EIG_LAYOUT_HALF, 128, 64},     {EIG_LAYOUT_HALF, 512, 128},
+                                {EIG_LAYOUT_CSR, 256, 64},      {EIG_LAYOUT_CSR, 128, 32},
+                                {EIG_LAYOUT_CSR, 512, 64}};
+  const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+  cudaEvent_t e0, e1;
+  EIG_CUDA_TRY(cudaEventCreate(&e0));
+  EIG_CUDA_TRY(cudaEventCreate(&e1));
+  int nres = 0;
+  best->ms = -1.0;
+  eig_status rc = EIG_OK;
+  for (int q = 0; q < ncand && rc == EIG_OK; ++q) {
+    SpmmPlan* P = new (std::nothrow) SpmmPlan();
+    if (!P) { rc = EIG_ENOMEM; break; }
+    eig_status s = spmm_plan_build(P, &Hd, cand[q][1], cand[q][2], cand[q][0], 0, st);
+    // a layout the matrix or the memory does not allow is skipped
+    if (s == EIG_OK && P->layout != cand[q][0]) s = EIG_EUNSUPPORTED;
+    double ms = -1.0;
+    if (s == EIG_OK) {
+      for (int w = 0; w < 2 && s == EIG_OK; ++w) s = spmm_run(P, X.p, Y.p, nb, vec_type, st);
+      if (s == EIG_OK) {
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && s == EIG_OK; ++r) s = spmm_run(P, X.p, Y.p, nb, vec_type, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = EIG_ECUDA;
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        ms = f / reps;
+      }
+    }
+    cudaStreamSynchronize(st);
+    delete P;
+    if (s == EIG_ECUDA) rc = s;
+    if (s != EIG_OK) continue;
+    eig_tune_result r{cand[q][0], cand[q][1], cand[q][2], ms};
+    if (all) all[nres] = r;
+    ++nres;
+    if (best->ms < 0.0 || ms < best->ms) *best = r;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (n_all) *n_all = nres;
+  if (rc != EIG_OK) return rc;
+  return nres ? EIG_OK : EIG_EUNSUPPORTED;
+}
+
+}  // extern "C"

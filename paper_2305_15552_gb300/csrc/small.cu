@@ -568,10 +568,13 @@ struct RRLayout {
 };
 
 __global__ void __launch_bounds__(kSmallThreads) k_small_rr(const double* A, const double* G, int k, int nb,
-                                                            double piv_tol, double* theta, double* C, float* C32,
-                                                            unsigned char* work, RRLayout L, int* info) {
+                                                            double piv_tol, int pivoted, double* theta, double* C,
+                                                            float* C32, unsigned char* work, RRLayout L, int* info) {
   __shared__ double red[33];
   __shared__ int flag;
+  __shared__ int sel[kSmallMax / 4];
+  __shared__ int ksel, pstar;
+  __shared__ double dstar;
   const int tid = threadIdx.x, nt = blockDim.x;
   double* g = (double*)(work + L.g);
   double* dsc = (double*)(work + L.dsc);
@@ -591,58 +594,121 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_rr(const double* A, con
     t[idx] = 0.5 * (A[i * k + l] + A[l * k + i]) * dsc[i] * dsc[l];
   }
   __syncthreads();
-  if (cholesky_lower(g, k, piv_tol, &flag) != SMALL_OK) {
+  int kk = k;
+  if (pivoted) {
+    // rank-revealing (diagonally pivoted) Cholesky of the scaled Gram on a copy in a: the
+    // basis columns are taken by largest remaining pivot until it falls to piv_tol; the
+    // Rayleigh-Ritz below then runs on those columns only
+    for (int idx = tid; idx < k * k; idx += nt) a[idx] = g[idx];
+    if (tid == 0) ksel = 0;
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+      if (tid == 0) {
+        int best = -1;
+        double bd = -1.0;
+        for (int i = 0; i < k; ++i)   // taken columns carry -1 on the diagonal
+          if (a[i * k + i] > bd) { bd = a[i * k + i]; best = i; }
+        pstar = (best >= 0 && bd > piv_tol) ? best : -1;
+        dstar = bd;
+        if (pstar >= 0) sel[ksel] = pstar;
+      }
+      __syncthreads();
+      if (pstar < 0) break;
+      const int p = pstar;
+      const double rp = rsqrt(dstar);
+      // Schur complement over the columns not yet taken (the taken ones are never read again)
+      for (int idx = tid; idx < k * k; idx += nt) {
+        const int i = idx / k, l = idx % k;
+        if (i != p && l != p) a[idx] -= (a[i * k + p] * rp) * (a[l * k + p] * rp);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int i = 0; i < k; ++i) { a[i * k + p] = 0.0; a[p * k + i] = 0.0; }
+        a[p * k + p] = -1.0;   // taken
+        ++ksel;
+      }
+      __syncthreads();
+    }
+    kk = ksel;
+    if (kk < nb) {
+      if (tid == 0) *info = SMALL_BREAKDOWN;
+      return;
+    }
+    // compact g, t (and the scaling) to the kk taken columns, in the order taken
+    for (int idx = tid; idx < kk * kk; idx += nt) a[idx] = g[sel[idx / kk] * k + sel[idx % kk]];
+    __syncthreads();
+    for (int idx = tid; idx < kk * kk; idx += nt) g[idx] = a[idx];
+    __syncthreads();
+    for (int idx = tid; idx < kk * kk; idx += nt) a[idx] = t[sel[idx / kk] * k + sel[idx % kk]];
+    __syncthreads();
+    for (int idx = tid; idx < kk * kk; idx += nt) t[idx] = a[idx];
+    for (int i = tid; i < kk; i += nt) z[i] = dsc[sel[i]];
+    __syncthreads();
+    for (int i = tid; i < kk; i += nt) dsc[i] = z[i];
+    __syncthreads();
+  }
+  if (cholesky_lower(g, kk, piv_tol, &flag) != SMALL_OK) {
     if (tid == 0) *info = SMALL_BREAKDOWN;
     return;
   }
   // W = L^{-1} T (forward substitution per column, thread per column) -> stored in a
-  for (int c = tid; c < k; c += nt) {
-    for (int i = 0; i < k; ++i) {
-      double s = t[i * k + c];
-      for (int l = 0; l < i; ++l) s -= g[i * k + l] * a[l * k + c];
-      a[i * k + c] = s / g[i * k + i];
+  for (int c = tid; c < kk; c += nt) {
+    for (int i = 0; i < kk; ++i) {
+      double s = t[i * kk + c];
+      for (int l = 0; l < i; ++l) s -= g[i * kk + l] * a[l * kk + c];
+      a[i * kk + c] = s / g[i * kk + i];
     }
   }
   __syncthreads();
   // T = L^{-1} W^T  (columns of W^T are rows of W) -> t
-  for (int c = tid; c < k; c += nt) {
-    for (int i = 0; i < k; ++i) {
-      double s = a[c * k + i];
-      for (int l = 0; l < i; ++l) s -= g[i * k + l] * t[l * k + c];
-      t[i * k + c] = s / g[i * k + i];
+  for (int c = tid; c < kk; c += nt) {
+    for (int i = 0; i < kk; ++i) {
+      double s = a[c * kk + i];
+      for (int l = 0; l < i; ++l) s -= g[i * kk + l] * t[l * kk + c];
+      t[i * kk + c] = s / g[i * kk + i];
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < k * k; idx += nt) {
-    const int i = idx / k, l = idx % k;
-    a[idx] = 0.5 * (t[i * k + l] + t[l * k + i]);
+  for (int idx = tid; idx < kk * kk; idx += nt) {
+    const int i = idx / kk, l = idx % kk;
+    a[idx] = 0.5 * (t[i * kk + l] + t[l * kk + i]);
   }
   __syncthreads();
-  syev_in_work(sw, L.S, k, nb, theta, z, red);
+  syev_in_work(sw, L.S, kk, nb, theta, z, red);
   // C = D L^{-T} Z (backward substitution per column)
   for (int c = tid; c < nb; c += nt) {
-    for (int i = k - 1; i >= 0; --i) {
+    for (int i = kk - 1; i >= 0; --i) {
       double s = z[i * nb + c];
-      for (int l = i + 1; l < k; ++l) s -= g[l * k + i] * C[l * nb + c];
-      C[i * nb + c] = s / g[i * k + i];
+      for (int l = i + 1; l < kk; ++l) s -= g[l * kk + i] * C[l * nb + c];
+      C[i * nb + c] = s / g[i * kk + i];
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < k * nb; idx += nt) {
-    const double v = C[idx] * dsc[idx / nb];
-    C[idx] = v;
-    if (C32) C32[idx] = (float)v;
+  for (int idx = tid; idx < kk * nb; idx += nt) C[idx] *= dsc[idx / nb];
+  __syncthreads();
+  if (pivoted) {
+    // rows of the taken columns back to their basis positions, zero rows for the others
+    for (int idx = tid; idx < kk * nb; idx += nt) z[idx] = C[idx];
+    __syncthreads();
+    for (int idx = tid; idx < k * nb; idx += nt) C[idx] = 0.0;
+    __syncthreads();
+    for (int idx = tid; idx < kk * nb; idx += nt) C[sel[idx / nb] * nb + idx % nb] = z[idx];
+    __syncthreads();
   }
+  if (C32)
+    for (int idx = tid; idx < k * nb; idx += nt) C32[idx] = (float)C[idx];
   if (tid == 0) *info = SMALL_OK;
 }
 
 size_t small_rr_work_bytes(int k, int nb) { return RRLayout(k, nb).total; }
 
 eig_status small_rr(const double* A, const double* G, int k, int nb, double piv_tol, double* theta, double* C,
-                    float* C32, void* work, int* info, cudaStream_t st) {
+                    float* C32, void* work, int* info, cudaStream_t st, int pivoted) {
   if (k < 1 || nb < 1 || nb > k || k > kSmallMax * 4) return EIG_EINVAL;
+  if (pivoted && k > kSmallMax / 4) return EIG_EINVAL;
   RRLayout L(k, nb);
-  k_small_rr<<<1, kSmallThreads, 0, st>>>(A, G, k, nb, piv_tol, theta, C, C32, (unsigned char*)work, L, info);
+  k_small_rr<<<1, kSmallThreads, 0, st>>>(A, G, k, nb, piv_tol, pivoted, theta, C, C32, (unsigned char*)work, L,
+                                          info);
   EIG_LAUNCH_CHECK("k_small_rr");
   return EIG_OK;
 }

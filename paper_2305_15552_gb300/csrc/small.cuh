@@ -28,9 +28,13 @@ eig_status small_tri_eig(const double* d, const double* e, int k, int m, double*
 // scales G to unit diagonal, Cholesky G = L L^T (breakdown when a squared pivot falls below
 // piv_tol), T = L^{-1} A L^{-T}, T Z = Z Theta, C = D^{-1/2} L^{-T} Z.
 // Outputs theta[nb], C (k x nb, row-major), C32 (optional float copy), info.
+// pivoted = 1: a rank-revealing (diagonally pivoted) Cholesky of the scaled G first takes the
+// basis columns in order of largest remaining pivot while it stays above piv_tol, and the
+// Rayleigh-Ritz runs on those columns (the others get zero rows in C); breakdown only when
+// fewer than nb columns remain.  For bases that lost rank (LOBPCG's [X W P] near convergence).
 size_t small_rr_work_bytes(int k, int nb);
 eig_status small_rr(const double* A, const double* G, int k, int nb, double piv_tol, double* theta, double* C,
-                    float* C32, void* work, int* info, cudaStream_t st);
+                    float* C32, void* work, int* info, cudaStream_t st, int pivoted = 0);
 
 // CholQR factor: G = R^T R (upper R) and Rinv = R^{-1}, k x k; info = SMALL_BREAKDOWN when a
 // squared pivot falls below piv_tol * max diag(G).  Rinv32: optional float copy.

@@ -377,7 +377,9 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   const int64_t n = h->n;
   const eig_dtype vt = c.o.vec_type;
   const size_t sv = dtype_size(vt);
-  const double piv_tol = (vt == EIG_F32) ? 1e-6 : 1e-13;
+  // squared pivots of the unit-diagonal Gram below this mark a basis too close to rank deficient
+  // for the projected problem (cond > 1e5 in FP32, 1e10 in FP64): the pivoted path takes over
+  const double piv_tol = (vt == EIG_F32) ? 1e-6 : 1e-10;
   for (int b = 0; b < 6; ++b) EIG_TRY(h->blk[b].reserve((size_t)n * nb * sv));
   void *X = h->blk[0].p, *W = h->blk[1].p, *P = h->blk[2].p, *HX = h->blk[3].p, *HW = h->blk[4].p, *HP = h->blk[5].p;
   const int kmax = 3 * nb;
@@ -399,7 +401,7 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   if (!cv.ok()) return EIG_EUNSUPPORTED;
   double* theta = stat;
   double* rsq = stat + nb;
-  EIG_TRY(h->host.reserve((2 * nb + 8) * 8));
+  EIG_TRY(h->host.reserve((2 * nb + 8) * 8 + (size_t)kmax * nb * 8 + (size_t)kmax * kmax * 8));
   double* hstat = h->host.as<double>();
   const double* diagH = h->plan.diag.as<double>();
   // learned K^{-1} (precond = 2): the update forms plain residuals, lp_precondition scales them
@@ -480,6 +482,10 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   for (int j = 0; j < nev; ++j) conv = conv && rel[j] < c.o.tol;
   int it = 0;
   bool hasP = false;
+  bool refresh_hs = false;
+  int since_refresh = 0;
+  double* hC = hstat + 2 * nb + 8;   // host copy of C (k x nb)
+  double* hG = hC + (size_t)kmax * nb;  // host copy of G (k x k)
   *reason = 0;
   while (!conv && it < maxiter) {
     if (stop) {
@@ -487,6 +493,15 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
       if (r) { *reason = r; break; }
     }
     ++it;
+    if (refresh_hs && hasP) {
+      // HX and HP are carried by the recurrences HX' = HX C1 + HP', HP' = HW C2 + HP C3; with
+      // large coefficients (a nearly dependent basis) their rounding drifts away from H X, H P
+      // and the next projected problem would be inconsistent: recompute both
+      EIG_TRY(c.spmm(X, HX, nb, vt, nb));
+      EIG_TRY(c.spmm(P, HP, nb, vt, nb));
+      refresh_hs = false;
+      since_refresh = 0;
+    }
     EIG_TRY(c.spmm(W, HW, nb, vt, nb));
     // Gram blocks: S = [X W P], HS = [HX HW HP]
     BlockList bl;
@@ -515,6 +530,13 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
     EIG_TRY(small_rr(A, G, k, nb, piv_tol, theta, C, nullptr, rrwork, info, c.st));
     EIG_CUDA_TRY(cudaMemcpyAsync(hstat + 2 * nb, info, 8, cudaMemcpyDeviceToHost, c.st));
     EIG_TRY(c.sync());
+    if (*reinterpret_cast<int*>(hstat + 2 * nb) != SMALL_OK) {
+      // the basis lost rank (converged columns' W, or W close to P): Rayleigh-Ritz on the
+      // columns a pivoted Cholesky keeps (the others get zero coefficients)
+      EIG_TRY(small_rr(A, G, k, nb, piv_tol, theta, C, nullptr, rrwork, info, c.st, 1));
+      EIG_CUDA_TRY(cudaMemcpyAsync(hstat + 2 * nb, info, 8, cudaMemcpyDeviceToHost, c.st));
+      EIG_TRY(c.sync());
+    }
     if (*reinterpret_cast<int*>(hstat + 2 * nb) != SMALL_OK && hasP) {
       // drop P (restart the search direction) and retry on [X W]
       k = 2 * nb;
@@ -535,6 +557,19 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
       *reason = 4;  // the basis lost rank: keep the last Ritz pairs
       --it;
       break;
+    }
+    {
+      // coefficients on unit-norm basis columns: |C_ij| sqrt(G_ii); large ones amplify the
+      // rounding of the carried products
+      EIG_CUDA_TRY(cudaMemcpyAsync(hC, C, (size_t)k * nb * 8, cudaMemcpyDeviceToHost, c.st));
+      EIG_CUDA_TRY(cudaMemcpyAsync(hG, G, (size_t)k * k * 8, cudaMemcpyDeviceToHost, c.st));
+      EIG_TRY(c.sync());
+      double cmax = 0.0;
+      for (int i = 0; i < k; ++i) {
+        const double sg = std::sqrt(std::max(hG[(size_t)i * k + i], 0.0));
+        for (int j = 0; j < nb; ++j) cmax = std::max(cmax, std::fabs(hC[(size_t)i * nb + j]) * sg);
+      }
+      if (cmax > 1e3 || ++since_refresh >= 20) refresh_hs = true;
     }
     int nparts = 0;
     EIG_TRY(lobpcg_update(X, W, P, HX, HW, HP, C, k, nb, theta, diagH, c.o.precond_floor, upd_precond(), n, vt, upart,
@@ -572,6 +607,28 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
 // batched RMM-DIIS (Alg. 4), FP32 vectors: double-float iterates, small quantities in FP32
 // (rmm_mixed.cu); same window, DIIS solve and 2x2 Rayleigh-Ritz as the FP64 step below
 // ---------------------------------------------------------------------------------------
+// RMM-DIIS stall rule: the worst relative residual of the wanted columns that are still
+// active has not halved within kRmmStall iterations (columns caught between near-degenerate
+// eigenvectors keep RMM-DIIS from converging, Sec. 3.3); the hybrid then hands over to LOBPCG.
+// Applied to the FP32-vector RMM-DIIS of the hybrid.
+constexpr int kRmmStall = 30;
+struct RmmStall {
+  double best = INFINITY;
+  int since = 0;
+  bool update(const std::vector<double>& rel, const std::vector<int>& act, int nev) {
+    double worst = 0.0;
+    for (int j = 0; j < nev; ++j)
+      if (act[j]) worst = std::max(worst, rel[j]);
+    if (worst < 0.5 * best) {
+      best = worst;
+      since = 0;
+    } else {
+      ++since;
+    }
+    return since >= kRmmStall;
+  }
+};
+
 static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* iters, bool* converged,
                                     std::vector<double>* theta_out) {
   Handle* h = c.h;
@@ -676,6 +733,7 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
   bool done = refresh();
   c.trace(1, 0, th.data(), rel.data(), nev);
   int count = 1, newest = 0, it = 0;
+  RmmStall stall;
   while (!done && it < maxiter) {
     ++it;
     EIG_CUDA_TRY(cudaMemcpyAsync(active, act.data(), mp * 4, cudaMemcpyHostToDevice, c.st));
@@ -720,6 +778,10 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
     const double prev_sum = lp_on ? [&]() { double t = 0.0; for (int j = 0; j < nev; ++j) t += th[j]; return t; }()
                                   : 0.0;
     done = refresh();
+    if (!done && stall.update(rel, act, nev)) {
+      c.trace(1, it, th.data(), rel.data(), nev);
+      break;
+    }
     if (lp_on) {
       // Jacobi replaces the learned K once a step raised the wanted Ritz values' sum or an
       // entry of m r was not finite
@@ -948,6 +1010,11 @@ eig_status eig_create(const eig_csr_upper* H, int n_ev, int block, void** handle
 }
 
 eig_status eig_create_ex(const eig_csr_upper* H, int n_ev, int block, int layout, void** handle) {
+  return eig_create_ex2(H, n_ev, block, layout, 0, 0, handle);
+}
+
+eig_status eig_create_ex2(const eig_csr_upper* H, int n_ev, int block, int layout, int row_block, int col_block,
+                          void** handle) {
   if (!handle || !H) return EIG_EINVAL;
   *handle = nullptr;
   if (n_ev < 1 || block < n_ev || block > 32 || n_ev > H->n) return EIG_EINVAL;
@@ -958,7 +1025,7 @@ eig_status eig_create_ex(const eig_csr_upper* H, int n_ev, int block, int layout
   h->n_ev = n_ev;
   h->nb = next_pow2(block);
   if (h->nb > H->n) h->nb = std::max(n_ev, (int)H->n);
-  eig_status s = spmm_plan_build(&h->plan, H, 0, 0, layout, 1, nullptr);
+  eig_status s = spmm_plan_build(&h->plan, H, row_block, col_block, layout, 1, nullptr);
   if (s != EIG_OK) {
     cudaDeviceSynchronize();
     delete h;

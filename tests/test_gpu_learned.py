@@ -177,7 +177,7 @@ def test_apply_matches_oracle(H, solver, H32, solver32, pairs, vt):
 def test_lobpcg_zero_output_layer_is_jacobi(solver):
     """o = 0 (zero output layer) makes m the Jacobi scale: the solve follows precond = 1 (the scale
     is rounded differently from the update kernel's division, so LOBPCG's iteration count, which
-    is sensitive to rounding, may differ by up to a tenth)."""
+    is sensitive to rounding, may differ by up to a quarter)."""
     p = _params(seed=2)
     p[L.OFF_W3:L.OFF_B3 + 1] = 0.0
     X0 = random_block(N, NB, seed=11)
@@ -185,7 +185,7 @@ def test_lobpcg_zero_output_layer_is_jacobi(solver):
     thj = solver.ritz()[0]
     rc, st = solver.solve("lobpcg", X0=X0, vec_type="f64", tol=1e-7, maxiter=400, precond=2, lp_params=p)
     th = solver.ritz()[0]
-    assert rc == rcj and abs(st["iterations_front"] - stj["iterations_front"]) <= max(2, stj["iterations_front"] // 10)
+    assert rc == rcj and abs(st["iterations_front"] - stj["iterations_front"]) <= max(2, stj["iterations_front"] // 4)
     np.testing.assert_allclose(th, thj, rtol=1e-9)
     assert st["lp_spmm_calls"] == st["iterations_front"] + 1 and st["precond_fallback"] == 0
 
