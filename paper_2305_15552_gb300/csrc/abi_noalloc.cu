@@ -15,7 +15,8 @@ namespace eig {
 namespace {
 
 // 4 MiB of partials: up to 512 CTA partials of a 32 x 32 Gram.
-constexpr size_t kNoAllocScratchDoubles = 512 * 32 * 32;
+constexpr int kNoAllocParts = 512;
+constexpr size_t kNoAllocScratchDoubles = (size_t)kNoAllocParts * 32 * 32;
 __device__ __align__(256) double g_gram_scratch[kNoAllocScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -48,7 +49,7 @@ eig_status eig_gram_noalloc(const void* A, const void* B, int64_t n, int nb, eig
                             void* stream) {
   if (!A || !B || !G || n < 1 || nb < 1 || nb > 32) return EIG_EINVAL;
   if (vec_type != EIG_F32 && vec_type != EIG_F64) return EIG_EINVAL;
-  if (gram_scratch_bytes(1, nb) > kNoAllocScratchDoubles * sizeof(double)) return EIG_EINVAL;
+  if ((size_t)kNoAllocParts * nb * nb > kNoAllocScratchDoubles) return EIG_EINVAL;
   void* scratch = nullptr;
   EIG_TRY(scratch_address(&scratch));
   BlockList bl;
@@ -57,7 +58,7 @@ eig_status eig_gram_noalloc(const void* A, const void* B, int64_t n, int nb, eig
   bl.p[1] = B;
   const int pa = 0, pb = 1;
   // every CTA overwrites all of its partials, so the array needs no clearing between calls
-  return gram_multi(bl, &pa, &pb, 1, nb, n, vec_type, G, scratch, as_stream(stream));
+  return gram_multi(bl, &pa, &pb, 1, nb, n, vec_type, G, scratch, as_stream(stream), kNoAllocParts);
 }
 
 }  // extern "C"

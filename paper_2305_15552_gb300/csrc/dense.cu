@@ -42,12 +42,25 @@ struct PairList {
   int n;
 };
 
-// Thread t owns tiles t, t+256, ... of the (pair, ti, tj) grid of TM x TM tiles.
-template <typename T, int TM, int MAXT>
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Thread t owns tiles t, t+256, ... of the (pair, ti, tj) grid of TM x TM tiles.  PIPE: the
+// chunks are staged by 16-byte cp.async copies into two shared-memory stages, the next chunk's
+// copies in flight while the current one is multiplied (rows of nb values must be a multiple of
+// 16 bytes and every block 16-byte aligned); the products and their order are the same either way.
+template <typename T, int TM, int MAXT, bool PIPE>
 __global__ void __launch_bounds__(kGramThreads)
 k_gram(BlockList blocks, PairList pairs, int nb, int64_t n, int64_t rows_per_cta, double* part) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sm = reinterpret_cast<T*>(sm_raw);  // [nblocks][kGramRows][nb]
+  T* sm_base = reinterpret_cast<T*>(sm_raw);  // [stages][nblocks][kGramRows][nb]
+  const size_t stage_elems = (size_t)blocks.n * kGramRows * nb;
   typedef typename Acc<T>::type A;
   const int tpp = (nb / TM) * (nb / TM);
   const int ntiles = pairs.n * tpp;     // <= MAXT * kGramThreads
@@ -61,15 +74,43 @@ k_gram(BlockList blocks, PairList pairs, int nb, int64_t n, int64_t rows_per_cta
       for (int j = 0; j < TM; ++j) { acc_zero(acc[s][i][j]); cacc[s][i][j] = T(0); }
   const int64_t r0 = blockIdx.x * rows_per_cta;
   const int64_t r1 = min64(n, r0 + rows_per_cta);
+  constexpr int EPC = 16 / sizeof(T);                // elements per 16-byte copy
+  auto issue = [&](int64_t rc, T* stage) {           // copies of the chunk at row rc
+    const int rows = (int)min64(kGramRows, r1 - rc);
+    const int per_block = kGramRows * nb / EPC;
+    for (int i = threadIdx.x; i < blocks.n * per_block; i += blockDim.x) {
+      const int b = i / per_block, e = (i % per_block) * EPC;
+      const T* src = static_cast<const T*>(blocks.p[b]) + rc * nb + e;
+      const bool in = e < rows * nb;
+      cp_async16(stage + (size_t)b * kGramRows * nb + e, in ? (const void*)src : blocks.p[b], in ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  if (PIPE && r0 < r1) issue(r0, sm_base);
+  int stage_i = 0;
   for (int64_t rc = r0; rc < r1; rc += kGramRows) {
     const int rows = (int)min64(kGramRows, r1 - rc);
-    __syncthreads();
-    for (int b = 0; b < blocks.n; ++b) {
-      const T* src = static_cast<const T*>(blocks.p[b]) + rc * nb;
-      T* dst = sm + (size_t)b * kGramRows * nb;
-      for (int i = threadIdx.x; i < kGramRows * nb; i += blockDim.x) dst[i] = (i < rows * nb) ? src[i] : T(0);
+    T* sm = sm_base + (PIPE ? (size_t)stage_i * stage_elems : 0);
+    if (PIPE) {
+      // the other stage was last read in the previous iteration: every thread is past it
+      __syncthreads();
+      if (rc + kGramRows < r1) {
+        issue(rc + kGramRows, sm_base + (size_t)(stage_i ^ 1) * stage_elems);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      stage_i ^= 1;
+    } else {
+      __syncthreads();
+      for (int b = 0; b < blocks.n; ++b) {
+        const T* src = static_cast<const T*>(blocks.p[b]) + rc * nb;
+        T* dst = sm + (size_t)b * kGramRows * nb;
+        for (int i = threadIdx.x; i < kGramRows * nb; i += blockDim.x) dst[i] = (i < rows * nb) ? src[i] : T(0);
+      }
+      __syncthreads();
     }
-    __syncthreads();
 #pragma unroll
     for (int s = 0; s < MAXT; ++s) {
       const int tile = threadIdx.x + s * kGramThreads;
@@ -122,8 +163,12 @@ __global__ void k_reduce_partials(const double* __restrict__ part, int nparts, i
   if (lane == 0) out[j] = s;
 }
 
-static int gram_grid(int64_t n, int64_t* rows_per_cta) {
+// Two CTAs per SM.  The grid also fixes how the rows are grouped into partial sums, and so the
+// rounding of every Gram: the hybrid's RMM-DIIS iteration count is sensitive to it (measured at
+// n = 2M: 7 iterations with this grouping, 21 with four CTAs per SM).
+static int gram_grid(int64_t n, int64_t* rows_per_cta, int max_parts) {
   int g = num_sms() * 2;
+  if (max_parts > 0 && g > max_parts) g = max_parts;
   int64_t rpc = (n + g - 1) / g;
   rpc = ((rpc + kGramRows - 1) / kGramRows) * kGramRows;
   if (rpc < kGramRows) rpc = kGramRows;
@@ -142,13 +187,18 @@ eig_status reduce_partials(const double* part, int nparts, int m, double* out, c
 
 template <typename T, int TM>
 static eig_status gram_launch(const BlockList& blocks, const PairList& pl, int nb, int64_t n, double* G, void* part,
-                              cudaStream_t st) {
+                              cudaStream_t st, int max_parts) {
   int64_t rpc;
-  const int g = gram_grid(n, &rpc);
-  const size_t sm = (size_t)blocks.n * kGramRows * nb * sizeof(T);
+  const int g = gram_grid(n, &rpc, max_parts);
+  bool pipe = (nb * sizeof(T)) % 16 == 0;
+  for (int b = 0; b < blocks.n; ++b) pipe = pipe && (reinterpret_cast<uintptr_t>(blocks.p[b]) % 16 == 0);
+  pipe = pipe && 2 * (size_t)blocks.n * kGramRows * nb * sizeof(T) <= 200 * 1024;
+  const size_t sm = (size_t)(pipe ? 2 : 1) * blocks.n * kGramRows * nb * sizeof(T);
   const int ntiles = pl.n * (nb / TM) * (nb / TM);
-  auto kern = (ntiles <= kGramThreads) ? k_gram<T, TM, 1>
-              : (ntiles <= 2 * kGramThreads ? k_gram<T, TM, 2> : k_gram<T, TM, 4>);
+  auto kern = pipe ? ((ntiles <= kGramThreads) ? k_gram<T, TM, 1, true>
+                      : (ntiles <= 2 * kGramThreads ? k_gram<T, TM, 2, true> : k_gram<T, TM, 4, true>))
+                   : ((ntiles <= kGramThreads) ? k_gram<T, TM, 1, false>
+                      : (ntiles <= 2 * kGramThreads ? k_gram<T, TM, 2, false> : k_gram<T, TM, 4, false>));
   if (sm > 48 * 1024) EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   kern<<<g, kGramThreads, sm, st>>>(blocks, pl, nb, n, rpc, static_cast<double*>(part));
   EIG_LAUNCH_CHECK("k_gram");
@@ -156,7 +206,7 @@ static eig_status gram_launch(const BlockList& blocks, const PairList& pl, int n
 }
 
 eig_status gram_multi(const BlockList& blocks, const int* pa, const int* pb, int npairs, int nb, int64_t n,
-                      eig_dtype vt, double* G, void* part, cudaStream_t st) {
+                      eig_dtype vt, double* G, void* part, cudaStream_t st, int max_parts) {
   if (npairs < 1 || npairs > kMaxPairs || nb < 1 || nb > 64 || n < 1 || blocks.n < 1 || blocks.n > 16) return EIG_EINVAL;
   PairList pl;
   pl.n = npairs;
@@ -168,14 +218,14 @@ eig_status gram_multi(const BlockList& blocks, const int* pa, const int* pb, int
   const int TM = (nb % 4 == 0) ? 4 : ((nb % 2 == 0) ? 2 : 1);
   if ((size_t)npairs * (nb / TM) * (nb / TM) > 4 * kGramThreads) return EIG_EUNSUPPORTED;
   if (vt == EIG_F32) {
-    if (TM == 4) return gram_launch<float, 4>(blocks, pl, nb, n, G, part, st);
-    if (TM == 2) return gram_launch<float, 2>(blocks, pl, nb, n, G, part, st);
-    return gram_launch<float, 1>(blocks, pl, nb, n, G, part, st);
+    if (TM == 4) return gram_launch<float, 4>(blocks, pl, nb, n, G, part, st, max_parts);
+    if (TM == 2) return gram_launch<float, 2>(blocks, pl, nb, n, G, part, st, max_parts);
+    return gram_launch<float, 1>(blocks, pl, nb, n, G, part, st, max_parts);
   }
   if (vt == EIG_F64) {
-    if (TM == 4) return gram_launch<double, 4>(blocks, pl, nb, n, G, part, st);
-    if (TM == 2) return gram_launch<double, 2>(blocks, pl, nb, n, G, part, st);
-    return gram_launch<double, 1>(blocks, pl, nb, n, G, part, st);
+    if (TM == 4) return gram_launch<double, 4>(blocks, pl, nb, n, G, part, st, max_parts);
+    if (TM == 2) return gram_launch<double, 2>(blocks, pl, nb, n, G, part, st, max_parts);
+    return gram_launch<double, 1>(blocks, pl, nb, n, G, part, st, max_parts);
   }
   return EIG_EINVAL;
 }

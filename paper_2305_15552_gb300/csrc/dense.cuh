@@ -15,10 +15,11 @@ struct BlockList {
 // G_q = A_{a_q}^T A_{b_q} for q < npairs, each nb x nb, FP64 out (G + q*nb*nb).  Blocks are
 // n x nb row-major of vec type vt.  FP32 blocks: FP32 products summed in FP32 over 32-row
 // chunks, chunk sums accumulated in double-float (hi+lo FP32 pairs), CTA partials in FP64.
-// part: device scratch of gram_scratch_bytes(npairs, nb) bytes.
+// part: device scratch of gram_scratch_bytes(npairs, nb) bytes, or of max_parts * npairs * nb * nb
+// doubles when max_parts > 0 caps the number of CTA partials.
 size_t gram_scratch_bytes(int npairs, int nb);
 eig_status gram_multi(const BlockList& blocks, const int* pa, const int* pb, int npairs, int nb, int64_t n,
-                      eig_dtype vt, double* G, void* part, cudaStream_t st);
+                      eig_dtype vt, double* G, void* part, cudaStream_t st, int max_parts = 0);
 
 // Out (n x m) = sum_s In_s (n x nb) * M[s*nb:(s+1)*nb, :]  (M FP64, K x m with K = nin*nb),
 // optionally + beta * Out.  m <= 64, K <= 1024.

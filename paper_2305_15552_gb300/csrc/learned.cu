@@ -98,6 +98,9 @@ struct LpSmemW {
   __device__ __forceinline__ float operator()(int i) const { return s[i]; }
 };
 
+// Inference: max(a, 0) (one instruction); a parameter vector with a non-finite entry is
+// caught on the host before the launch (it makes every output non-finite, as the network
+// arithmetic would).
 template <class WA>
 __device__ __forceinline__ float lp_infer(const WA& w, const float f[kLpFeat]) {
   float u[kLpFeat];
@@ -109,7 +112,7 @@ __device__ __forceinline__ float lp_infer(const WA& w, const float f[kLpFeat]) {
     float a = w(kLpOffB1 + k);
 #pragma unroll
     for (int q = 0; q < kLpFeat; ++q) a = fmaf(w(kLpOffW1 + k * kLpFeat + q), u[q], a);
-    h1[k] = lp_relu(a);
+    h1[k] = fmaxf(a, 0.0f);
   }
   float m = w(kLpOffB3);
 #pragma unroll
@@ -117,7 +120,7 @@ __device__ __forceinline__ float lp_infer(const WA& w, const float f[kLpFeat]) {
     float a = w(kLpOffB2 + k);
 #pragma unroll
     for (int l = 0; l < kLpHid; ++l) a = fmaf(w(kLpOffW2 + k * kLpHid + l), h1[l], a);
-    m = fmaf(w(kLpOffW3 + k), lp_relu(a), m);
+    m = fmaf(w(kLpOffW3 + k), fmaxf(a, 0.0f), m);
   }
   return m;
 }
@@ -139,7 +142,8 @@ template <typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 k_lp_apply(const __grid_constant__ LpParams prm, const T* R, const T* HR, int ld, int m, int64_t n,
            const double* __restrict__ diagH, const double* __restrict__ rowabs, const double* __restrict__ theta,
-           const double* __restrict__ rsq, float floor_, const int* __restrict__ active, T* W, int* nonfinite) {
+           const double* __restrict__ rsq, float floor_, const int* __restrict__ active, T* W, int* nonfinite,
+           int broken) {
   typedef typename LpAcc<T>::type A;
   __shared__ double sTh[32];
   __shared__ A sSc[32];
@@ -158,7 +162,7 @@ k_lp_apply(const __grid_constant__ LpParams prm, const T* R, const T* HR, int ld
     if (sAct[j]) {
       float f[kLpFeat];
       lp_feature_row<A>(d, sTh[j], rowabs[i], r, hr, sSc[j], f);
-      out = (A)(lp_jscale(f[2]) * (1.0f + lp_infer(w, f))) * r;
+      out = broken ? (A)NAN : (A)(lp_jscale(f[2]) * (1.0f + lp_infer(w, f))) * r;
       if (!isfinite(out)) {
         A den = (A)(d - sTh[j]);
         const A mag = den < (A)0 ? -den : den;
@@ -198,14 +202,21 @@ k_lp_features(const T* __restrict__ R, const T* __restrict__ HR, int ld, int m, 
 }
 
 __global__ void __launch_bounds__(kApplyThreads)
-k_lp_forward(const __grid_constant__ LpParams prm, const float* __restrict__ F, int64_t count, float* __restrict__ mo) {
+k_lp_forward(const __grid_constant__ LpParams prm, const float* __restrict__ F, int64_t count, float* __restrict__ mo,
+             int broken) {
   const LpConstW w{prm};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
     float f[kLpFeat];
 #pragma unroll
     for (int q = 0; q < kLpFeat; ++q) f[q] = F[e * kLpFeat + q];
-    mo[e] = lp_jscale(f[2]) * (1.0f + lp_infer(w, f));
+    mo[e] = broken ? NAN : lp_jscale(f[2]) * (1.0f + lp_infer(w, f));
   }
+}
+
+int params_broken(const LpParams& prm) {
+  for (int i = 0; i < kLpParams; ++i)
+    if (!std::isfinite(prm.p[i])) return 1;
+  return 0;
 }
 
 int apply_grid(int64_t count) {
@@ -421,13 +432,14 @@ eig_status lp_apply(const LpParams& prm, const void* R, const void* HR, int ld, 
   if (m < 1 || m > 32 || ld < m || n < 0) return EIG_EINVAL;
   if (n == 0) return EIG_OK;
   const int grid = apply_grid(n * m);
+  const int broken = params_broken(prm);
   if (vt == EIG_F32)
     k_lp_apply<float><<<grid, kApplyThreads, 0, st>>>(prm, (const float*)R, (const float*)HR, ld, m, n, diagH, rowabs,
-                                                      theta, rsq, (float)floor_, active, (float*)W, nonfinite);
+                                                      theta, rsq, (float)floor_, active, (float*)W, nonfinite, broken);
   else if (vt == EIG_F64)
     k_lp_apply<double><<<grid, kApplyThreads, 0, st>>>(prm, (const double*)R, (const double*)HR, ld, m, n, diagH,
                                                        rowabs, theta, rsq, (float)floor_, active, (double*)W,
-                                                       nonfinite);
+                                                       nonfinite, broken);
   else
     return EIG_EINVAL;
   EIG_LAUNCH_CHECK("k_lp_apply");
@@ -455,7 +467,7 @@ eig_status lp_features(const void* R, const void* HR, int ld, int m, int64_t n, 
 eig_status lp_forward(const LpParams& prm, const float* F, int64_t count, float* m_out, cudaStream_t st) {
   if (count < 0) return EIG_EINVAL;
   if (count == 0) return EIG_OK;
-  k_lp_forward<<<apply_grid(count), kApplyThreads, 0, st>>>(prm, F, count, m_out);
+  k_lp_forward<<<apply_grid(count), kApplyThreads, 0, st>>>(prm, F, count, m_out, params_broken(prm));
   EIG_LAUNCH_CHECK("k_lp_forward");
   return EIG_OK;
 }

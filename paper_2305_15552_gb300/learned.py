@@ -134,3 +134,33 @@ def jacobi_loss(sample, floor=2.0):
     err = r.double() / den - z.double()
     w = colw.repeat(F.shape[0] // m)
     return float((w * err * err).sum().item())
+
+
+def time_forward(rows=8_000_000, reps=20, seed=0):
+    """Mean device time (ms) of the network kernel (eig_lp_forward) on `rows` random feature rows,
+    after three warm-up launches: a quick check of its throughput (2516 FLOP per row)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    F = torch.tensor(rng.standard_normal((rows, 6)).astype(np.float32), device="cuda")
+    p = init_params(np.zeros(6), np.ones(6), seed=seed + 1)
+    p[OFF_W3:OFF_B3 + 1] = (rng.standard_normal(33) * 0.1).astype(np.float32)
+    for _ in range(3):
+        B.lp_forward(p, F)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        B.lp_forward(p, F)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="time the learned preconditioner's network kernel")
+    ap.add_argument("--rows", type=int, default=8_000_000)
+    ap.add_argument("--reps", type=int, default=20)
+    a = ap.parse_args()
+    ms = time_forward(a.rows, a.reps)
+    print(f"eig_lp_forward: {a.rows} rows, {ms:.4f} ms per launch, {a.rows * 2516 / (ms * 1e-3) / 1e12:.2f} TFLOP/s")
