@@ -150,6 +150,16 @@ EIG_API eig_status eig_spmm_plan_info(const void* plan, eig_spmm_info* info);
  * Supported (matrix, vector) types: (F32,F32), (F64,F64), (BF16,F32), (F32,F64), (BF16,F64). */
 EIG_API eig_status eig_spmm(void* plan, const void* X, void* Y, int nb, eig_dtype vec_type, void* stream);
 
+/* One step of the Chebyshev recurrence (Alg. 3, Eq. chebypoly) fused into the product's epilogue:
+ * Y = alpha (H X - c X) - Qp, or Y = alpha (H X - c X) when first != 0 (Qp unused), and Y = X on
+ * columns with active[j] == 0 (device int[nb]; locked columns).  The same double arithmetic on
+ * the same rounded H X as the product followed by a separate elementwise pass, with one read of X,
+ * Qp and one write of Y.  Mirrored layout, nb = 8, 16 or 32, FP32 vectors with FP32 values or
+ * FP64 vectors with FP64 / FP32 values; other cases return EIG_EUNSUPPORTED (compute H X with
+ * eig_spmm and the step separately).  Alignment rule of eig_spmm. */
+EIG_API eig_status eig_spmm_cheb(void* plan, const void* X, void* Y, int nb, eig_dtype vec_type, const void* Qp,
+                                 const int* active, double alpha, double c, int first, void* stream);
+
 /* Gram product G = A^T B (Eq. rreig's S^T S / S^T H S; Eq. bgs's V^T W).  A, B: device, row-major
  * n x nb of vec_type (F32 or F64), nb <= 64; G: device FP64 nb x nb (row-major).  FP32 inputs:
  * products in FP32, 32-row partial sums accumulated in double-float (two FP32 words), CTA

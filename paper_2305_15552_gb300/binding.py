@@ -74,6 +74,8 @@ _SIGS = {
                                           C.POINTER(C.c_void_p)]),
     "eig_spmm_plan_info": (C.c_int, [C.c_void_p, C.POINTER(SpmmInfo)]),
     "eig_spmm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "eig_spmm_cheb": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_double, C.c_double, C.c_int, C.c_void_p]),
     "eig_gram": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "eig_gram_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "eig_cholqr2": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
@@ -223,6 +225,20 @@ class SpmmPlan:
             Y = torch.empty_like(X)
         check(self._lib.eig_spmm(self._h, _ptr(X), _ptr(Y), int(X.shape[1]), vec_dtype(X), stream_ptr(stream)),
               "eig_spmm")
+        return Y
+
+    def spmm_cheb(self, X, alpha, c, Qp=None, active=None, Y=None, stream=None):
+        """eig_spmm_cheb: Y = alpha (H X - c X) - Qp (Qp None: first step), Y = X on inactive
+        columns (active: torch int32 on the device, default all active)."""
+        import torch
+        assert X.is_cuda and X.is_contiguous() and X.dim() == 2 and X.shape[0] == self.n
+        if Y is None:
+            Y = torch.empty_like(X)
+        if active is None:
+            active = torch.ones(X.shape[1], dtype=torch.int32, device=X.device)
+        check(self._lib.eig_spmm_cheb(self._h, _ptr(X), _ptr(Y), int(X.shape[1]), vec_dtype(X),
+                                      None if Qp is None else _ptr(Qp), _ptr(active), float(alpha), float(c),
+                                      1 if Qp is None else 0, stream_ptr(stream)), "eig_spmm_cheb")
         return Y
 
     def close(self):

@@ -97,4 +97,11 @@ eig_status eig_spmm(void* plan, const void* X, void* Y, int nb, eig_dtype vec_ty
   return eig::spmm_run(static_cast<eig::SpmmPlan*>(plan), X, Y, nb, vec_type, eig::as_stream(stream));
 }
 
+eig_status eig_spmm_cheb(void* plan, const void* X, void* Y, int nb, eig_dtype vec_type, const void* Qp,
+                         const int* active, double alpha, double c, int first, void* stream) {
+  if (!plan || !X || !Y || !active) return EIG_EINVAL;
+  return eig::spmm_run_cheb(static_cast<eig::SpmmPlan*>(plan), X, Y, nb, vec_type, Qp, active, alpha, c, first,
+                            eig::as_stream(stream));
+}
+
 }  // extern "C"

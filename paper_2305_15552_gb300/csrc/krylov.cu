@@ -657,10 +657,17 @@ eig_status run_chebfsi(Ctx& c, const double* X0, int x0c, int* iters, bool* conv
     else k_cheb<double><<<g, 256, 0, c.st>>>((const double*)HQ, (const double*)Q, nullptr, (double*)Wb, act_d, cc, ee, 1, nb, n);
     EIG_LAUNCH_CHECK("k_cheb");
     for (int j = 2; j <= deg; ++j) {
-      EIG_TRY(c.spmm(Wb, HW, nb, vt, nact));
-      if (vt == EIG_F32) k_cheb<float><<<g, 256, 0, c.st>>>((const float*)HW, (const float*)Wb, (const float*)Qp, (float*)Y, act_d, cc, ee, 0, nb, n);
-      else k_cheb<double><<<g, 256, 0, c.st>>>((const double*)HW, (const double*)Wb, (const double*)Qp, (double*)Y, act_d, cc, ee, 0, nb, n);
-      EIG_LAUNCH_CHECK("k_cheb");
+      // Y = 2 (H W - c W) / e - Qp: fused into the SpMM's epilogue where the layout allows it
+      // (one read of W and Qp, one write of Y), else the product then the elementwise step
+      const eig_status fs = c.spmm_cheb(Wb, Y, nb, vt, nact, Qp, act_d, 2.0 / ee, cc, 0);
+      if (fs == EIG_EUNSUPPORTED) {
+        EIG_TRY(c.spmm(Wb, HW, nb, vt, nact));
+        if (vt == EIG_F32) k_cheb<float><<<g, 256, 0, c.st>>>((const float*)HW, (const float*)Wb, (const float*)Qp, (float*)Y, act_d, cc, ee, 0, nb, n);
+        else k_cheb<double><<<g, 256, 0, c.st>>>((const double*)HW, (const double*)Wb, (const double*)Qp, (double*)Y, act_d, cc, ee, 0, nb, n);
+        EIG_LAUNCH_CHECK("k_cheb");
+      } else {
+        EIG_TRY(fs);
+      }
       std::swap(Qp, Wb);  // Qp <- W
       std::swap(Wb, Y);   // W <- Y
     }

@@ -182,6 +182,30 @@ eig_status Ctx::spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_
   return EIG_OK;
 }
 
+eig_status Ctx::spmm_cheb(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols, const void* Qp,
+                          const int* active, double alpha, double cshift, int first) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (o.timing) {
+    EIG_CUDA_TRY(cudaEventCreate(&a));
+    EIG_CUDA_TRY(cudaEventCreate(&b));
+    EIG_CUDA_TRY(cudaEventRecord(a, st));
+  }
+  const eig_status r = spmm_run_cheb(&h->plan, X, Y, nb, vt, Qp, active, alpha, cshift, first, st);
+  if (r != EIG_OK) {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return r;
+  }
+  if (o.timing) {
+    EIG_CUDA_TRY(cudaEventRecord(b, st));
+    spmm_ev.emplace_back(a, b);
+  }
+  s->spmm_calls += 1;
+  s->spmv_count += spmv_cols;
+  s->spmm_bytes += h->plan.algorithmic_bytes(nb, dtype_size(vt));
+  return EIG_OK;
+}
+
 Ctx::~Ctx() {
   for (auto& e : spmm_ev) {
     cudaEventDestroy(e.first);

@@ -53,6 +53,9 @@ struct Ctx {
   eig_stats* s;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
   eig_status spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols);
+  // spmm with a fused Chebyshev step (spmm_run_cheb); EIG_EUNSUPPORTED leaves Y untouched
+  eig_status spmm_cheb(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols, const void* Qp,
+                       const int* active, double alpha, double cshift, int first);
   // one convergence-history row (opts.trace), count <= n_ev values of theta and relres
   void trace(int phase, int it, const double* th, const double* rel, int count) {
     if (!o.trace || s->trace_rows >= o.trace_cap) return;

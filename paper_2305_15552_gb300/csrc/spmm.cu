@@ -482,6 +482,10 @@ template <typename T, typename V, int NB> eig_status tiled_launch(SpmmPlan* P, c
 template <typename T, typename V, int NB> eig_status mirror_launch(SpmmPlan* P, const T* X, T* Y, cudaStream_t st);
 
 template <typename T, typename V, int NB>
+eig_status mirror_launch_cheb(SpmmPlan* P, const T* X, T* Y, const T* Qp, const int* active, double alpha, double c,
+                              int first, cudaStream_t st);
+
+template <typename T, typename V, int NB>
 static eig_status launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st) {
   // gather-only kernel on the mirrored copy (its stages fit in shared memory for every
   // supported shape; it needs no scratch)
@@ -550,6 +554,31 @@ eig_status spmm_run(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, c
   if (nb != 1 && nb != 2 && nb != 4 && nb != 8 && nb != 16 && nb != 32) return EIG_EINVAL;
   EIG_TRY(P->scratch.reserve(spmm_scratch_bytes(P, nb, vt)));
   return spmm_run_with_scratch(P, X, Y, nb, vt, P->scratch.p, st);
+}
+
+}  // namespace eig
+
+namespace eig {
+
+eig_status spmm_run_cheb(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, const void* Qp, const int* active,
+                         double alpha, double c, int first, cudaStream_t st) {
+  if (!P || !X || !Y || !active || (!first && !Qp)) return EIG_EINVAL;
+  if (!P->mirrored || (nb != 8 && nb != 16 && nb != 32)) return EIG_EUNSUPPORTED;
+  const size_t es = vt == EIG_F64 ? 8 : 4;
+  const size_t al = std::min<size_t>(16, (size_t)nb * es);
+  const uintptr_t m = (uintptr_t)X | (uintptr_t)Y | (first ? 0 : (uintptr_t)Qp);
+  if (m % al) return EIG_EINVAL;
+#define EIG_CHEB_NB(T, V)                                                                                            \
+  switch (nb) {                                                                                                     \
+    case 8: return mirror_launch_cheb<T, V, 8>(P, (const T*)X, (T*)Y, (const T*)Qp, active, alpha, c, first, st);  \
+    case 16: return mirror_launch_cheb<T, V, 16>(P, (const T*)X, (T*)Y, (const T*)Qp, active, alpha, c, first, st); \
+    default: return mirror_launch_cheb<T, V, 32>(P, (const T*)X, (T*)Y, (const T*)Qp, active, alpha, c, first, st); \
+  }
+  if (vt == EIG_F32 && P->val_type == EIG_F32) { EIG_CHEB_NB(float, float) }
+  if (vt == EIG_F64 && P->val_type == EIG_F64) { EIG_CHEB_NB(double, double) }
+  if (vt == EIG_F64 && P->val_type == EIG_F32) { EIG_CHEB_NB(double, float) }
+#undef EIG_CHEB_NB
+  return EIG_EUNSUPPORTED;
 }
 
 }  // namespace eig

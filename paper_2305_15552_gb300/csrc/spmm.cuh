@@ -94,5 +94,11 @@ eig_status spmm_run(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, c
 size_t spmm_scratch_bytes(const SpmmPlan* P, int nb, eig_dtype vt);
 eig_status spmm_run_with_scratch(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, void* scratch,
                                  cudaStream_t st);
+// One Chebyshev step fused into the SpMM's epilogue (mirrored layout, nb 8 / 16 / 32; FP32 or
+// FP64 vectors): Y = alpha (H X - c X) - Qp (no Qp when first), Y = X on columns with
+// active[j] == 0 (device int[nb]).  EIG_EUNSUPPORTED for other layouts / shapes: the caller
+// then runs the SpMM and the elementwise step separately.
+eig_status spmm_run_cheb(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, const void* Qp, const int* active,
+                         double alpha, double c, int first, cudaStream_t st);
 
 }  // namespace eig

@@ -537,9 +537,19 @@ template <typename T, int NB> struct MirrorShape {
   static constexpr int GPW = kMGroups / WARPS;
 };
 
-template <typename T, typename V, int NB>
+// Fused epilogue of a Chebyshev step (Alg. 3, Eq. chebypoly): Y = a (H X - c X) - Qp (first: no
+// Qp), and Y = X on inactive (locked) columns; the same double arithmetic on the same rounded
+// product H X as the separate elementwise pass.
+struct MirrorEpi {
+  const void* Qp;
+  const int* active;
+  double a, c;
+  int first;
+};
+
+template <typename T, typename V, int NB, bool CHEB = false>
 __global__ void __launch_bounds__(MirrorShape<T, NB>::WARPS * 32, MirrorShape<T, NB>::MINB)
-k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_bulk) {
+k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_bulk, MirrorEpi epi) {
   typedef MirrorShape<T, NB> Sh;
   constexpr int EPL = Sh::EPL, L = Sh::L, RPI = Sh::RPI, SB = Sh::SB, M = Sh::M, JJ = Sh::JJ;
   constexpr int RB = Sh::RB, NCOPY = Sh::NCOPY, LINE = Sh::LINE, WARPS = Sh::WARPS, GPW = Sh::GPW;
@@ -707,6 +717,21 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
         out.v[e] = v;
       }
       const int64_t r = r0 + g * kMG + rsub + sb * RPI;
+      if (CHEB && sp == 0 && r < a.n) {
+        const T* Qp = static_cast<const T*>(epi.Qp);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int jc = q * EPL + e;
+          const T wv = X[r * NB + jc];
+          if (!epi.active[jc]) {
+            out.v[e] = wv;
+          } else {
+            double yv = epi.a * ((double)out.v[e] - epi.c * (double)wv);
+            if (!epi.first) yv -= (double)Qp[r * NB + jc];
+            out.v[e] = (T)yv;
+          }
+        }
+      }
       if (sp == 0 && r < a.n) VecIO<T, EPL>::st(Y + r * NB + q * EPL, out);
     }
   }
@@ -803,10 +828,54 @@ eig_status mirror_launch(SpmmPlan* P, const T* X, T* Y, cudaStream_t st) {
   const int xj_bulk = (Sh::RB % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
   auto kern = k_spmm_mirror<T, V, NB>;
   EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  kern<<<(unsigned)P->nRB, Sh::WARPS * 32, sm, st>>>(a, X, Y, xj_bulk);
+  kern<<<(unsigned)P->nRB, Sh::WARPS * 32, sm, st>>>(a, X, Y, xj_bulk, MirrorEpi());
   EIG_LAUNCH_CHECK("k_spmm_mirror");
   return EIG_OK;
 }
+
+// The Chebyshev-step variant (same kernel, fused epilogue).
+template <typename T, typename V, int NB>
+eig_status mirror_launch_cheb(SpmmPlan* P, const T* X, T* Y, const T* Qp, const int* active, double alpha, double c,
+                              int first, cudaStream_t st) {
+  typedef MirrorShape<T, NB> Sh;
+  int dev = 0, maxsm = 0;
+  EIG_CUDA_TRY(cudaGetDevice(&dev));
+  EIG_CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t sm = mirror_smem<T, V, NB>(P);
+  if (sm > (size_t)maxsm) return EIG_EUNSUPPORTED;
+  MirrorArgs a;
+  a.n = P->n;
+  a.capq = P->m_capq;
+  a.chunk_ptr = P->m_chunk_ptr.as<int64_t>();
+  a.chunks = P->m_chunks.as<MirrorChunk>();
+  a.mcol = P->m_col.as<uint8_t>();
+  a.mval = P->m_val.p;
+  a.mgq = P->m_gq.as<uint8_t>();
+  a.err = P->err.as<int>();
+  MirrorEpi epi;
+  epi.Qp = Qp;
+  epi.active = active;
+  epi.a = alpha;
+  epi.c = c;
+  epi.first = first;
+  const int xj_bulk = (Sh::RB % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
+  auto kern = k_spmm_mirror<T, V, NB, true>;
+  EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<(unsigned)P->nRB, Sh::WARPS * 32, sm, st>>>(a, X, Y, xj_bulk, epi);
+  EIG_LAUNCH_CHECK("k_spmm_mirror_cheb");
+  return EIG_OK;
+}
+
+#define EIG_MIRROR_CHEB_INST(T, V)                                                                               \
+  template eig_status mirror_launch_cheb<T, V, 8>(SpmmPlan*, const T*, T*, const T*, const int*, double, double,  \
+                                                  int, cudaStream_t);                                            \
+  template eig_status mirror_launch_cheb<T, V, 16>(SpmmPlan*, const T*, T*, const T*, const int*, double, double, \
+                                                   int, cudaStream_t);                                           \
+  template eig_status mirror_launch_cheb<T, V, 32>(SpmmPlan*, const T*, T*, const T*, const int*, double, double, \
+                                                   int, cudaStream_t);
+EIG_MIRROR_CHEB_INST(float, float)
+EIG_MIRROR_CHEB_INST(double, double)
+EIG_MIRROR_CHEB_INST(double, float)
 
 #define EIG_MIRROR_INST(T, V)                                                           \
   template eig_status mirror_launch<T, V, 1>(SpmmPlan*, const T*, T*, cudaStream_t);    \

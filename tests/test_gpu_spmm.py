@@ -208,3 +208,43 @@ def test_bench_size_sampled_rows(bench_matrix, layout, nb):
     absH = CSRUpper(H.n, H.rowptr, H.col, np.abs(H.values_f64()), "f64")
     bound = O.sym_upper_matmul(absH, np.abs(X.astype(np.float64)))[rows]
     assert np.all(err <= 1000 * 2.0 ** -24 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("storage,dt,nb", [("f32", "f32", 16), ("f32", "f32", 8), ("f64", "f64", 8),
+                                           ("f32", "f64", 32)])
+def test_spmm_cheb_fused_step_matches_definition(storage, dt, nb):
+    """eig_spmm_cheb (Chebyshev step in the SpMM epilogue, Alg. 3) against the oracle's product and
+    Eq. (chebypoly) evaluated in FP64: later steps with Qp, the first step without, and locked
+    columns copied through."""
+    import torch
+    from paper_2305_15552_gb300.binding import SpmmPlan
+    H = ci_matrix(5003, 120, 64, seed=4, storage=storage)
+    P = SpmmPlan(H, layout="mirrored")
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((H.n, nb))
+    Q = rng.standard_normal((H.n, nb))
+    Xd, Qd = torch.tensor(X, dtype=tdt, device="cuda"), torch.tensor(Q, dtype=tdt, device="cuda")
+    Xr = Xd.double().cpu().numpy()
+    Qr = Qd.double().cpu().numpy()
+    HX = O.sym_upper_matmul(H, Xr)
+    act = np.ones(nb, dtype=np.int32)
+    act[1] = 0
+    actd = torch.tensor(act, device="cuda")
+    alpha, c = 2.0 / 7.5, 3.25
+    tol = 3e-6 if dt == "f32" else 1e-12
+    Y = P.spmm_cheb(Xd, alpha, c, Qp=Qd, active=actd).double().cpu().numpy()
+    want = alpha * (HX - c * Xr) - Qr
+    want[:, 1] = Xr[:, 1]
+    np.testing.assert_allclose(Y, want, rtol=0, atol=tol * np.abs(want).max())
+    assert np.array_equal(Y[:, 1], Xr[:, 1])
+    Y1 = P.spmm_cheb(Xd, 1.0 / 7.5, c).double().cpu().numpy()
+    np.testing.assert_allclose(Y1, (HX - c * Xr) / 7.5, rtol=0, atol=tol * np.abs(HX).max())
+    # equal to the unfused product followed by the elementwise step
+    HXg = P.spmm(Xd).double().cpu().numpy()
+    Yu = alpha * (HXg - c * Xr) - Qr
+    Yu[:, 1] = Xr[:, 1]
+    # (the device may contract a multiply-add: a last-bit difference, seen only near cancellation)
+    np.testing.assert_allclose(Y, Yu.astype(np.float32 if dt == "f32" else np.float64), rtol=2e-7 if dt == "f32" else 1e-15,
+                               atol=(1e-7 if dt == "f32" else 1e-15) * np.abs(Yu).max())
+    P.close()
