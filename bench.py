@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--n", "--rows", dest="n", type=int, default=2_000_000,
+                    help="matrix dimension (--rows: the spelling to use under torchrun, whose own options "
+                         "--nnodes / --nproc-per-node make --n ambiguous)")
     ap.add_argument("--nnz-per-row", type=float, default=400)
     ap.add_argument("--block-pattern", type=int, default=256)
     ap.add_argument("--nev", type=int, default=8)
