@@ -333,6 +333,12 @@ EIG_API eig_status eig_ritz(void* handle, double* theta, double* X, double* relr
 EIG_API eig_status eig_create_ex2(const eig_csr_upper* H, int n_ev, int block, int layout, int row_block,
                                   int col_block, void** handle);
 
+/* eig_create_ex for count matrices Hs[0..count) with one n_ev, block and layout: handles[i]
+ * (caller array of count pointers).  All or nothing: on an error every handle already created
+ * is destroyed, all entries are NULL, and the first error is returned. */
+EIG_API eig_status eig_create_batch(const eig_csr_upper* Hs, int count, int n_ev, int block, int layout,
+                                    void** handles);
+
 /* Solves count independent instances (handles from eig_create*) with one method.  opts: NULL =
  * defaults for all; otherwise opts[i] for instance i when per_instance_opts != 0, else opts[0]
  * for all (an X0 given there is then shared).  `threads` host threads (0 = min(count, 16)) take

@@ -95,6 +95,7 @@ _SIGS = {
     "eig_lp_param_count": (C.c_int, []),
     "eig_create_ex2": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.POINTER(C.c_void_p)]),
+    "eig_create_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "eig_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                   C.c_void_p]),
     "eig_autotune_spmm": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -562,3 +563,21 @@ def autotune_spmm(H, nb, vec_type="f32", reps=5):
         return {"layout": LAYOUT_NAMES.get(r.layout, r.layout), "row_block": r.row_block, "col_block": r.col_block,
                 "ms": r.ms}
     return d(best), [d(allr[i]) for i in range(na.value)]
+
+
+def create_batch(Hs, n_ev, block, layout="auto"):
+    """eig_create_batch: Solver objects for the matrices Hs (all created, or none and an error)."""
+    import numpy as np
+    lib = load()
+    arrs = [(np.ascontiguousarray(H.rowptr), np.ascontiguousarray(H.col), np.ascontiguousarray(H.val)) for H in Hs]
+    sts = (CsrUpper * max(len(Hs), 1))()
+    for i, (H, (rp, cl, vl)) in enumerate(zip(Hs, arrs)):
+        sts[i] = csr_struct(rp, cl, vl, H.storage, H.n, False)
+    hs = (C.c_void_p * max(len(Hs), 1))()
+    check(lib.eig_create_batch(sts, len(Hs), int(n_ev), int(block), layout_code(layout), hs), "eig_create_batch")
+    out = []
+    for i, H in enumerate(Hs):
+        S = Solver.__new__(Solver)
+        S._lib, S._h, S.n, S.n_ev = lib, C.c_void_p(hs[i]), H.n, n_ev
+        out.append(S)
+    return out

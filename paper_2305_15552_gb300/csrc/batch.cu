@@ -42,6 +42,22 @@ using namespace eig;
 
 extern "C" {
 
+eig_status eig_create_batch(const eig_csr_upper* Hs, int count, int n_ev, int block, int layout, void** handles) {
+  if (count < 0 || (count > 0 && (!Hs || !handles))) return EIG_EINVAL;
+  for (int i = 0; i < count; ++i) handles[i] = nullptr;
+  for (int i = 0; i < count; ++i) {
+    const eig_status s = eig_create_ex(&Hs[i], n_ev, block, layout, &handles[i]);
+    if (s != EIG_OK) {
+      for (int j = 0; j < i; ++j) {
+        eig_destroy(handles[j]);
+        handles[j] = nullptr;
+      }
+      return s;
+    }
+  }
+  return EIG_OK;
+}
+
 eig_status eig_solve_batch(void* const* handles, int count, eig_method method, const eig_opts* opts,
                            int per_instance_opts, int threads, eig_status* status, eig_stats* stats) {
   if (count < 0 || (count > 0 && !handles)) return EIG_EINVAL;

@@ -62,9 +62,9 @@ def test_batch_equals_single_solves_and_oracle(instances):
 
 
 def test_batch_more_instances_than_threads_and_one_thread(instances):
-    from paper_2305_15552_gb300.binding import Solver, solve_batch
+    from paper_2305_15552_gb300.binding import create_batch, solve_batch
     Hs, X0s = instances
-    Ss = [Solver(H, NEV, NB) for H in Hs[:3]]
+    Ss = create_batch(Hs[:3], NEV, NB)
     o = dict(vec_type="f64", tol=1e-5, maxiter=500)
     rc, sts, _ = solve_batch(Ss, "lobpcg", X0s=X0s[:3], opts=o, threads=1)
     assert rc == 0 and sts == [0, 0, 0]
