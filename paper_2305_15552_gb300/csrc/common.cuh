@@ -81,14 +81,15 @@ struct DevBuf {
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// SM count of the device current at the first call (thread-safe initialisation: concurrent
+// solves of a batch call this from several host threads).
 inline int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = []() {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
 }
 

@@ -479,11 +479,8 @@ eig_status lp_grad(const float* params, const float* F, const float* r, const fl
   if (m < 1 || n < 0 || !params || !out || !workspace) return EIG_EINVAL;
   const int grid = grad_grid();
   const size_t smem = kGradSmemFloats * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    EIG_CUDA_TRY(cudaFuncSetAttribute(k_lp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  // set on every call: the attribute belongs to the current device
+  EIG_CUDA_TRY(cudaFuncSetAttribute(k_lp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_lp_grad<<<grid, kGradThreads, smem, st>>>(params, F, r, z, colw, n, m, (double*)workspace);
   EIG_LAUNCH_CHECK("k_lp_grad");
   return reduce_partials((const double*)workspace, grid, kGradOut, out, st);
