@@ -68,3 +68,19 @@ def test_random_block_seeded():
     a = random_block(100, 4, 9)
     b = random_block(100, 4, 9)
     assert np.array_equal(a, b) and a.shape == (100, 4)
+
+
+def test_family_member_is_h0_plus_g_v_on_the_same_pattern():
+    from gen import family_perturbation, family_member
+    H0 = ci_matrix(3000, 80, 64, seed=5, storage="f64")
+    V = family_perturbation(H0, seed=9)
+    assert V.shape == (H0.nnz,) and abs(V.std() - 0.1) < 0.01
+    np.testing.assert_array_equal(V, family_perturbation(H0, seed=9))
+    assert not np.array_equal(V, family_perturbation(H0, seed=10))
+    Hg = family_member(H0, V, 0.75)
+    assert Hg.rowptr is H0.rowptr and Hg.col is H0.col
+    np.testing.assert_array_equal(Hg.values_f64(), H0.values_f64() + 0.75 * V)
+    np.testing.assert_array_equal(family_member(H0, V, 0.0).values_f64(), H0.values_f64())
+    H32 = family_member(H0, V, 1.25, storage="f32")
+    assert H32.val.dtype == np.float32
+    np.testing.assert_array_equal(H32.val, (H0.values_f64() + 1.25 * V).astype(np.float32))

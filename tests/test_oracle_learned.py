@@ -189,3 +189,43 @@ def test_apply_falls_back_to_jacobi_on_non_finite():
     p[L.OFF_B3] = 0.5
     np.testing.assert_allclose(L.apply(p, F, R, H.diagonal_f64(), th),
                                1.5 * O.jacobi_apply(H.diagonal_f64(), th, R, 2.0), rtol=1e-15)
+
+
+def test_oracle_training_improves_on_jacobi():
+    """The whole recipe in FP64 on a small family: samples from perturbed eigenvectors, the
+    network started as the Jacobi K (zero output layer), Adam on the loss gradient; the training
+    loss falls below the Jacobi K's."""
+    from gen import family_perturbation, family_member
+    H0 = ci_matrix(600, 60, 64, seed=11, storage="f64")
+    V = family_perturbation(H0, seed=12)
+    rng = np.random.default_rng(13)
+    samples = []
+    for g in (0.6, 0.9, 1.2):
+        H = family_member(H0, V, g)
+        D = O.to_dense(H)
+        w, Z = np.linalg.eigh(D)
+        Xs = Z[:, :6]
+        X = np.linalg.qr(Xs + 0.05 * rng.standard_normal(Xs.shape))[0]
+        th = np.einsum("ij,ij->j", X, D @ X)
+        R = L.residual(H, X, th)
+        F = L.features(H, th, R)
+        Zt, c = L.correction_target(X, Xs)
+        samples.append((F, R, Zt, c))
+    Fall = np.concatenate([s[0].reshape(-1, 6) for s in samples])
+    p = np.zeros(L.N_PARAMS)
+    p[0:6], p[6:12] = Fall.mean(axis=0), np.maximum(Fall.std(axis=0), 1e-6)
+    p[L.OFF_W1:L.OFF_B1] = rng.standard_normal(192) * np.sqrt(2 / 6)
+    p[L.OFF_W2:L.OFF_B2] = rng.standard_normal(1024) * np.sqrt(2 / 32)
+    jac = np.mean([L.loss(p, *s)[0] for s in samples])          # zero output layer: the Jacobi K
+    jac_direct = np.mean([((R * L.jacobi_scale(F[..., 2]) - Zt) ** 2 * c).sum() / (c > 0).sum()
+                          for F, R, Zt, c in samples])
+    assert jac == pytest.approx(jac_direct, rel=1e-12)
+    m1, m2 = np.zeros(L.N_PARAMS), np.zeros(L.N_PARAMS)
+    t = 0
+    for ep in range(60):
+        for s in samples:
+            t += 1
+            _, g = L.loss_grad(p, *s)
+            p, m1, m2 = L.adam_step(p, g, m1, m2, t, 3e-3)
+    trained = np.mean([L.loss(p, *s)[0] for s in samples])
+    assert trained < 0.9 * jac, (trained, jac)
