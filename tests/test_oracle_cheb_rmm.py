@@ -123,3 +123,23 @@ def test_planted_mistakes_are_caught():
     a_old = (r2 @ (r2 - r1)) / ((r2 - r1) @ (r2 - r1))
     a_wrong = (r1 @ (r2 - r1)) / ((r2 - r1) @ (r2 - r1))
     assert abs(a_wrong - a_old) > 1e-3
+
+
+def test_certification_bounds_contain_the_exact_eigenvalue():
+    """Residual bound |lambda - theta| <= ||r|| and Kato-Temple |lambda - theta| <= ||r||^2 / gap
+    (gap to the rest of the spectrum) for Rayleigh quotients of perturbed eigenvectors, against the
+    dense spectrum."""
+    H = ci_matrix(400, 40, 64, seed=8, storage="f64")
+    D = O.to_dense(H)
+    w, V = np.linalg.eigh(D)
+    rng = np.random.default_rng(2)
+    for j, eps in [(0, 1e-3), (3, 1e-2), (7, 1e-4)]:
+        z = V[:, j] + eps * rng.standard_normal(H.n)
+        z /= np.linalg.norm(z)
+        th = z @ D @ z
+        rn = O.residual_bound(H, np.array([th]), z[:, None])[0]
+        assert rn == pytest.approx(np.linalg.norm(D @ z - th * z), rel=1e-10)
+        k = np.argmin(np.abs(w - th))
+        assert abs(w[k] - th) <= rn * (1 + 1e-12)
+        gap = np.min(np.abs(np.delete(w, k) - th))
+        assert abs(w[k] - th) <= O.kato_temple(rn, gap) * (1 + 1e-9)
