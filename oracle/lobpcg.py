@@ -11,7 +11,13 @@ Readings:
 * K^{-1} is the Jacobi preconditioner of oracle.precond (precond="none" gives K = I);
 * the Rayleigh-Ritz step works on the numerically independent part of span(S)
   (oracle.blocks.rayleigh_ritz_projected), which is the exact pencil solution whenever
-  S^T S is nonsingular.
+  S^T S is nonsingular;
+* the recurrences of Eqs. (upd1)-(upd2) are exact in exact arithmetic but carry rounding: once
+  the Rayleigh-Ritz coefficients on unit-norm basis columns exceed 1e3 (a nearly dependent S,
+  Sec. 2.3's ill-conditioned pencil), or every 20 iterations, H X and H P are recomputed by
+  their definition (products not counted in `spmm`, which counts the method's own products).
+  Without this the Ritz values of long runs drifted below the spectrum (to -1e76 on a
+  20,000-row CI matrix from a random start).
 """
 import numpy as np
 
@@ -39,6 +45,8 @@ def lobpcg(H, X0, nev, tol=1e-6, maxiter=500, precond="jacobi", floor=2.0, U=Non
     hist = [dict(it=0, theta=theta.copy(), relres=relres.copy())]
     conv = bool(np.all(relres[:nev] < tol))
     it = 0
+    since = 0
+    refreshed = 0
     while not conv and it < maxiter:
         if stop is not None and stop(it, theta, relres):
             break
@@ -60,9 +68,16 @@ def lobpcg(H, X0, nev, tol=1e-6, maxiter=500, precond="jacobi", floor=2.0, U=Non
             HPn = HPn + HP @ C3
         X, HX = S @ C, HS @ C
         P, HP = Pn, HPn
+        since += 1
+        cmax = np.max(np.abs(C) * np.linalg.norm(S, axis=0)[:, None])
+        if cmax > 1e3 or since >= 20:
+            HX = sym_upper_matmul(H, X, U)
+            HP = sym_upper_matmul(H, P, U)
+            since = 0
+            refreshed += 1
         R = HX - X * theta[None, :]
         relres = np.linalg.norm(R, axis=0) / np.abs(theta)
         hist.append(dict(it=it, theta=theta.copy(), relres=relres.copy()))
         conv = bool(np.all(relres[:nev] < tol))
     return EigResult(theta=theta, X=X, relres=relres, converged=conv, iterations=it, spmm=spmm,
-                     spmv=spmm * nb, HX=HX, history=hist)
+                     spmv=spmm * nb, HX=HX, history=hist, extra=dict(refreshed=refreshed))

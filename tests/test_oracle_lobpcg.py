@@ -1,5 +1,6 @@
 """Pins for LOBPCG (Alg. 2) and the Jacobi preconditioner."""
 import numpy as np
+import scipy.sparse as sp
 
 import oracle as O
 from gen import laplacian_kron, laplacian_kron_eigs, ci_matrix, random_block, principal_submatrix, pad_rows
@@ -40,3 +41,18 @@ def test_jacobi_precond_floor():
     # (0-0.95) -> -0.95; (1-0.95) = 0.05 -> floored to 0.1; (5-0.95) = 4.05
     np.testing.assert_allclose(W[:, 0], [1 / -0.95, 1 / 0.1, 1 / 4.05])
     np.testing.assert_allclose(W[:, 1], [1 / -2.0, 1 / -1.0, 1 / 3.0])
+
+
+def test_lobpcg_and_lanczos_match_eigsh_at_20000():
+    """The plain FP64 workload (n = 20,000, ~100 nnz/row, block pattern 64, n_ev = 5, block 8):
+    the oracle's LOBPCG and Lanczos against scipy's ARPACK (eigsh, smallest algebraic)."""
+    import scipy.sparse.linalg as sla
+    H = ci_matrix(20000, 100, 64, seed=1, storage="f64")
+    U = O.to_scipy_upper(H)
+    A = (U + U.T - sp.diags(U.diagonal())).tocsr()
+    ref = np.sort(sla.eigsh(A, k=5, which="SA", tol=1e-12)[0])
+    r = O.lobpcg(H, random_block(H.n, 8, 3), 5, tol=1e-8, maxiter=500, U=U)
+    assert r.converged
+    np.testing.assert_allclose(np.sort(r.theta[:5]), ref, rtol=1e-9, atol=1e-12)
+    lz = O.lanczos(H, np.random.default_rng(4).standard_normal(H.n), 5, tol=1e-8)
+    np.testing.assert_allclose(np.sort(lz.theta[:5]), ref, rtol=1e-9, atol=1e-12)
