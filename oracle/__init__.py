@@ -30,6 +30,6 @@ from .lobpcg import lobpcg
 from .chebfsi import chebfsi, lambda_ub_estimate, cheb_filter
 from .rmmdiis import rmmdiis, diis_coefficients, rr2
 from .hybrid import hybrid, switch_tau
-from .certify import true_relres, residual_bound, kato_temple
+from .certify import true_relres, residual_bound, kato_temple, missed_eigenvalues
 
 __all__ = [n for n in dir() if not n.startswith("_")]

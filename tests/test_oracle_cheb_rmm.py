@@ -143,3 +143,13 @@ def test_certification_bounds_contain_the_exact_eigenvalue():
         assert abs(w[k] - th) <= rn * (1 + 1e-12)
         gap = np.min(np.abs(np.delete(w, k) - th))
         assert abs(w[k] - th) <= O.kato_temple(rn, gap) * (1 + 1e-9)
+
+
+def test_missed_eigenvalue_guard():
+    """Lanczos from three random starts confirms a correct lowest-five result and finds the
+    eigenvalue a planted mistake left out (a result holding lambda_1, lambda_3..lambda_6)."""
+    H = ci_matrix(1500, 60, 64, seed=4, storage="f64")
+    w = np.linalg.eigvalsh(O.to_dense(H))
+    assert O.missed_eigenvalues(H, w[:5], 5).size == 0
+    missed = O.missed_eigenvalues(H, np.r_[w[0], w[2:6]], 5)
+    assert missed.size >= 1 and np.min(np.abs(missed - w[1])) < 1e-8 * np.abs(w[:6]).max()
