@@ -365,6 +365,15 @@ typedef struct {
 EIG_API eig_status eig_autotune_spmm(const eig_csr_upper* H, int nb, eig_dtype vec_type, int reps,
                                      eig_tune_result* best, eig_tune_result* all, int* n_all, void* stream);
 
+/* The Chebyshev degree d of Alg. 3 for this handle's matrix: runs the ChebFSI solve (opts from
+ * base, NULL = defaults; cheb_degree and timing overridden) once per degrees[i] and returns in
+ * *best_degree the degree of the fastest solve that converged (time_ms_total); ms[i] and
+ * converged[i] (may be NULL) receive each run's time and status.  The handle keeps the result
+ * of the last run.  EIG_ENOT_CONVERGED (and *best_degree = 0) when no degree converged.
+ * Synchronises base->stream. */
+EIG_API eig_status eig_autotune_cheb(void* handle, const int* degrees, int count, const eig_opts* base,
+                                     int* best_degree, double* ms, int* converged);
+
 /* ------------------------------------------------------------------------------------ *
  * Learned per-row preconditioner (a replacement for K of Eq. (wblock))                 *
  * ------------------------------------------------------------------------------------ *

@@ -96,6 +96,8 @@ _SIGS = {
     "eig_create_ex2": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.POINTER(C.c_void_p)]),
     "eig_create_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "eig_autotune_cheb": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.c_void_p,
+                                    C.c_void_p]),
     "eig_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                   C.c_void_p]),
     "eig_autotune_spmm": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -581,3 +583,20 @@ def create_batch(Hs, n_ev, block, layout="auto"):
         S._lib, S._h, S.n, S.n_ev = lib, C.c_void_p(hs[i]), H.n, n_ev
         out.append(S)
     return out
+
+
+def autotune_cheb(solver, degrees, X0=None, **opts):
+    """eig_autotune_cheb: the Chebyshev degree with the fastest converged ChebFSI solve on this
+    solver's matrix.  Returns (best degree or 0, [ms per degree], [converged per degree])."""
+    import numpy as np
+    lib = load()
+    o, keeps, _ = _make_opts(lib, X0, opts, solver.n_ev)
+    d = np.ascontiguousarray(degrees, dtype=np.int32)
+    ms = np.zeros(d.size)
+    cv = np.zeros(d.size, dtype=np.int32)
+    best = C.c_int(0)
+    rc = lib.eig_autotune_cheb(solver._h, _ptr(d), int(d.size), C.byref(o), C.byref(best), _ptr(ms), _ptr(cv))
+    del keeps
+    if rc not in (EIG_OK, EIG_ENOT_CONVERGED):
+        raise EigError(rc, "eig_autotune_cheb")
+    return best.value, ms.tolist(), cv.tolist()

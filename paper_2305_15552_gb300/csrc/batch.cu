@@ -179,4 +179,30 @@ eig_status eig_autotune_spmm(const eig_csr_upper* H, int nb, eig_dtype vec_type,
   return nres ? EIG_OK : EIG_EUNSUPPORTED;
 }
 
+eig_status eig_autotune_cheb(void* handle, const int* degrees, int count, const eig_opts* base, int* best_degree,
+                             double* ms, int* converged) {
+  if (!handle || !degrees || count < 1 || !best_degree) return EIG_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (degrees[i] < 1) return EIG_EINVAL;
+  *best_degree = 0;
+  double best = -1.0;
+  for (int i = 0; i < count; ++i) {
+    eig_opts o;
+    if (base) o = *base;
+    else eig_default_opts(&o);
+    o.cheb_degree = degrees[i];
+    o.timing = 1;
+    eig_stats st;
+    const eig_status s = eig_solve(handle, EIG_CHEBFILTER, &o, &st);
+    if (s != EIG_OK && s != EIG_ENOT_CONVERGED) return s;
+    if (ms) ms[i] = st.time_ms_total;
+    if (converged) converged[i] = (s == EIG_OK) ? 1 : 0;
+    if (s == EIG_OK && (best < 0.0 || st.time_ms_total < best)) {
+      best = st.time_ms_total;
+      *best_degree = degrees[i];
+    }
+  }
+  return *best_degree ? EIG_OK : EIG_ENOT_CONVERGED;
+}
+
 }  // extern "C"

@@ -93,3 +93,23 @@ def test_autotune_picks_a_buildable_shape_that_solves_the_same(instances):
     np.testing.assert_allclose(th, S.ritz()[0], rtol=1e-7)
     S.close()
     assert rc == rc0 == 0
+
+
+def test_autotune_cheb_degree():
+    """eig_autotune_cheb picks, among the degrees tried, the fastest ChebFSI solve that converged;
+    a solve with that degree reaches the dense eigenvalues."""
+    from paper_2305_15552_gb300.binding import Solver, autotune_cheb
+    from gen import principal_submatrix, pad_rows
+    H = ci_matrix(3000, 100, 64, seed=1, storage="f64")
+    lam = np.linalg.eigvalsh(O.to_dense(H))[:NEV]
+    X0 = pad_rows(O.lowest_eigpairs(O.to_dense(principal_submatrix(H, 300)), NB)[1], H.n)
+    S = Solver(H, NEV, NB)
+    degs = [6, 10, 14]
+    best, ms, cv = autotune_cheb(S, degs, X0=X0, vec_type="f64")
+    assert best in degs and cv[degs.index(best)] == 1
+    assert ms[degs.index(best)] == min(m for m, c in zip(ms, cv) if c)
+    rc, _ = S.solve("chebfilter", X0=X0, vec_type="f64", cheb_degree=best)
+    th = S.ritz()[0]
+    S.close()
+    assert rc == 0
+    np.testing.assert_allclose(th, lam, rtol=1e-6)
