@@ -28,7 +28,7 @@ from .lanczos import lanczos
 from .block_lanczos import block_lanczos
 from .lobpcg import lobpcg
 from .chebfsi import chebfsi, lambda_ub_estimate, cheb_filter
-from .rmmdiis import rmmdiis, diis_coefficients, rr2
+from .rmmdiis import rmmdiis, diis_coefficients, diis_extrapolate, rr2
 from .hybrid import hybrid, switch_tau
 from .certify import true_relres, residual_bound, kato_temple, missed_eigenvalues
 

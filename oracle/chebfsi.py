@@ -53,6 +53,12 @@ def lambda_ub_estimate(H, v, steps=10, U=None):
     return float(th[-1] + beta[k - 1] * abs(Q[-1, -1])), k
 
 
+def cheb_step(HW, W, Qp, c, e):
+    """One step of the three-term recurrence of Eq. (chebypoly) on (H - cI)/e:
+    T_{j}(t) = 2 t T_{j-1}(t) - T_{j-2}(t), i.e. Y = 2 (H W - c W) / e - Q_prev."""
+    return 2.0 * (HW - c * W) / e - Qp
+
+
 def cheb_filter(H, Q, HQ, deg, c, e, active=None, U=None):
     """Y = T_deg((H - cI)/e) Q on the active columns (others returned unchanged) and
     H Y for the active columns' last recurrence input.  Returns (Y, products)."""
@@ -66,7 +72,7 @@ def cheb_filter(H, Q, HQ, deg, c, e, active=None, U=None):
     for _ in range(2, deg + 1):
         HW = sym_upper_matmul(H, W, U)
         products += 1
-        Y = 2.0 * (HW - c * W) / e - Qp
+        Y = cheb_step(HW, W, Qp, c, e)
         Qp, W = W, Y
     Y = Q.copy()
     Y[:, act] = W

@@ -50,6 +50,16 @@ def diis_coefficients(rs):
     return np.concatenate([a, [1.0 - a.sum()]])
 
 
+def diis_extrapolate(xs, rs, s_max):
+    """x~ of Eq. (xsum) for one eigenvector, normalised: the DIIS combination (Eqs. alphasum,
+    rmm) of the newest s = min(len(xs), s_max) iterates, i in [l - s, l - 1] (the reading of the
+    garbled sum limits).  xs, rs: iterate and residual histories, oldest first."""
+    s = min(len(xs), s_max)
+    alpha = diis_coefficients(rs[-s:])
+    xt = sum(al * np.asarray(xv, dtype=np.float64) for al, xv in zip(alpha, xs[-s:]))
+    return xt / np.linalg.norm(xt)
+
+
 def rr2(x, r, Hx, Hr):
     """Smaller eigenpair of the 2x2 pencil (W^T H W, W^T W), W = (x, r) (Eq. rr).
     Returns (theta, g) with g^T (W^T W) g = 1 and g_1 <= 0.  Falls back to the Rayleigh quotient of x
@@ -98,10 +108,7 @@ def rmmdiis(H, X0, tol=1e-6, maxiter=200, s_max=10, HX0=None, U=None, precond="n
             if it == 1:
                 Xt[:, a] = X[:, j]
             else:
-                s = min(len(xh[j]), s_max)
-                alpha = diis_coefficients(rh[j][-s:])
-                xt = sum(al * xv for al, xv in zip(alpha, xh[j][-s:]))
-                Xt[:, a] = xt / np.linalg.norm(xt)
+                Xt[:, a] = diis_extrapolate(xh[j], rh[j], s_max)
         HXt = sym_upper_matmul(H, Xt, U)
         tht = np.einsum("ij,ij->j", Xt, HXt) / np.einsum("ij,ij->j", Xt, Xt)
         Rt = HXt - Xt * tht[None, :]

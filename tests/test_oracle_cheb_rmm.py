@@ -1,4 +1,6 @@
 """Pins for ChebFSI (Alg. 3), RMM-DIIS (Alg. 4) and the hybrid switch (Eq. switchtau)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -110,19 +112,104 @@ def test_hybrid_ci_vs_dense():
     assert r.extra["front_iterations"] == 3 and r.extra["switch"] == "after"
 
 
-def test_planted_mistakes_are_caught():
-    """Wrong-sign recurrence and a DIIS that drops the constraint both fail their pins."""
+def _window_fixture():
+    path = os.path.join(os.path.dirname(__file__), "golden", "rmmdiis_window.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    xs = [np.array([1.0, 0.0]), np.array([0.0, 1.0]), np.array([1.0, 1.0])]
+    rs = [np.array([1.0, 1.0]), np.array([1.0, 0.0]), np.array([0.0, 2.0])]
+    return xs, rs, [(int(r[0]), np.array([float(r[1]), float(r[2])])) for r in rows]
+
+
+def check_diis_window():
+    """tests/golden/rmmdiis_window.txt: x~ of Eq. (xsum) over the newest s iterates, worked by
+    hand for s_max = 1, 2, 3 on three two-dimensional histories."""
+    xs, rs, want = _window_fixture()
+    for s_max, xt in want:
+        np.testing.assert_allclose(O.diis_extrapolate(xs, rs, s_max), xt, rtol=0, atol=1e-14)
+
+
+def test_diis_window_hand_worked():
+    check_diis_window()
+
+
+def check_cheb_filter_diagonal(deg=5):
     d = np.linspace(-1.5, 9.0, 40)
-    t = (d - 4.0) / 3.0
-    # a recurrence with + Q instead of - Q
-    W1, W0 = t, np.ones_like(t)
-    wrong = 2 * t * W1 + W0
-    assert np.abs(wrong - cheb_scalar(2, t)).max() > 1.0
+    H = diagonal_matrix(d)
+    c, e = 4.0, 3.0
+    Q = np.eye(40)
+    Y, _ = O.cheb_filter(H, Q, O.sym_upper_matmul(H, Q), deg, c, e)
+    np.testing.assert_allclose(np.diag(Y), cheb_scalar(deg, (d - c) / e), rtol=1e-12, atol=1e-12)
+
+
+def check_diis_two_vector():
     rng = np.random.default_rng(1)
     r1, r2 = rng.standard_normal(50), rng.standard_normal(50)
     a_old = (r2 @ (r2 - r1)) / ((r2 - r1) @ (r2 - r1))
-    a_wrong = (r1 @ (r2 - r1)) / ((r2 - r1) @ (r2 - r1))
-    assert abs(a_wrong - a_old) > 1e-3
+    np.testing.assert_allclose(O.diis_coefficients([r1, r2]), [a_old, 1 - a_old], rtol=1e-12)
+
+
+def check_rmmdiis_converges_to_lowest():
+    H = laplacian_kron([9, 10, 11])
+    lam, V = O.lowest_eigpairs(O.to_dense(H), 3)
+    r = O.rmmdiis(H, V + 1e-3 * random_block(H.n, 3, 7), tol=1e-9, maxiter=400, s_max=20)
+    assert r.converged
+    np.testing.assert_allclose(r.theta, lam, rtol=1e-10)
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Mistakes planted in the oracle itself (its module functions replaced by wrong variants)
+    fail the pins above: a recurrence with + Q_prev (Eq. chebypoly), a DIIS window over the
+    oldest instead of the newest iterates, DIIS coefficients without the affine constraint of
+    Eq. (alphasum), and the larger root of the 2x2 pencil (Eq. rr)."""
+    import importlib
+    C = importlib.import_module("oracle.chebfsi")   # the modules (the package re-exports functions
+    R = importlib.import_module("oracle.rmmdiis")   # of the same names)
+    check_cheb_filter_diagonal()
+    check_diis_window()
+    check_diis_two_vector()
+    check_rmmdiis_converges_to_lowest()
+
+    with monkeypatch.context() as m:
+        m.setattr(C, "cheb_step", lambda HW, W, Qp, c, e: 2.0 * (HW - c * W) / e + Qp)
+        with pytest.raises(AssertionError):
+            check_cheb_filter_diagonal()
+
+    def oldest_window(xs, rs, s_max):
+        s = min(len(xs), s_max)
+        alpha = R.diis_coefficients(rs[:s])
+        xt = sum(al * xv for al, xv in zip(alpha, xs[:s]))
+        return xt / np.linalg.norm(xt)
+    with monkeypatch.context() as m:
+        m.setattr(R, "diis_extrapolate", oldest_window)
+        m.setattr(O, "diis_extrapolate", oldest_window)
+        with pytest.raises(AssertionError):
+            check_diis_window()
+
+    def unconstrained(rs):
+        A = np.stack([np.asarray(r, dtype=np.float64) for r in rs], axis=1)
+        a, *_ = np.linalg.lstsq(A, A[:, -1], rcond=None)   # fits the newest residual instead
+        return a
+    with monkeypatch.context() as m:
+        m.setattr(R, "diis_coefficients", unconstrained)
+        m.setattr(O, "diis_coefficients", unconstrained)
+        with pytest.raises(AssertionError):
+            check_diis_two_vector()
+        with pytest.raises(AssertionError):
+            check_diis_window()
+
+    real_rr2 = R.rr2
+
+    def larger_root(x, r, Hx, Hr):
+        A = np.array([[x @ Hx, x @ Hr], [r @ Hx, r @ Hr]])
+        B = np.array([[x @ x, x @ r], [r @ x, r @ r]])
+        import scipy.linalg as sla
+        w, G = sla.eigh(0.5 * (A + A.T), 0.5 * (B + B.T))
+        return float(w[1]), G[:, 1]
+    with monkeypatch.context() as m:
+        m.setattr(R, "rr2", larger_root)
+        with pytest.raises(AssertionError):
+            check_rmmdiis_converges_to_lowest()
+    assert R.rr2 is real_rr2
 
 
 def test_certification_bounds_contain_the_exact_eigenvalue():
