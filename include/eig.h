@@ -291,6 +291,12 @@ typedef struct {
                            /* the wanted Ritz values, or a non-finite m r): LOBPCG in the low 16   */
                            /* bits, RMM-DIIS in the high 16 bits                                    */
   int64_t lp_spmm_calls;   /* products H r spent on the learned preconditioner's features           */
+  /* SpMM calls, CUDA-event time (timing = 1) and algorithmic bytes per product shape, index  */
+  /* 6 * (vector type is EIG_F64) + log2(nb): e.g. 4 = FP32 vectors nb 16, 3 = FP32 nb 8,     */
+  /* 9 = FP64 vectors nb 8                                                                     */
+  int64_t spmm_calls_by_shape[12];
+  double spmm_ms_by_shape[12];
+  double spmm_bytes_by_shape[12];
 } eig_stats;
 
 /* Fills *o with the defaults documented in eig_opts. */

@@ -20,7 +20,7 @@ Parity pins: every function is checked in tests/test_oracle_*.py against closed
 forms (Kronecker-sum Laplacian spectra, Chebyshev T_m(cos t) = cos(m t), 2x2 pencil
 roots, two-vector DIIS), brute-force dense diagonalisation and invariants.
 """
-from .spmm import sym_upper_matmul, to_scipy_upper, to_dense, spmv_count_per_spmm
+from .spmm import sym_upper_matmul, to_scipy_upper, to_dense, spmv_count_per_spmm, parallel_upper, ParallelUpper
 from .dense import lowest_eigpairs, eigh_sorted
 from .blocks import gram, cholqr, cholqr2, rayleigh_ritz, rayleigh_ritz_projected, orthonormal_basis
 from .precond import jacobi_apply

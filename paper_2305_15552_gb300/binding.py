@@ -59,7 +59,18 @@ class Stats(C.Structure):
                 ("last_tau", C.c_double), ("max_relres", C.c_double), ("time_ms_total", C.c_double),
                 ("time_ms_spmm", C.c_double), ("time_ms_front", C.c_double), ("time_ms_rmm", C.c_double),
                 ("spmm_timed", C.c_int64), ("spmm_bytes", C.c_double), ("trace_rows", C.c_int),
-                ("iterations_fallback", C.c_int), ("precond_fallback", C.c_int), ("lp_spmm_calls", C.c_int64)]
+                ("iterations_fallback", C.c_int), ("precond_fallback", C.c_int), ("lp_spmm_calls", C.c_int64),
+                ("spmm_calls_by_shape", C.c_int64 * 12), ("spmm_ms_by_shape", C.c_double * 12),
+                ("spmm_bytes_by_shape", C.c_double * 12)]
+
+
+def stats_dict(stats):
+    """eig_stats as a dict (the per-shape arrays as lists)."""
+    out = {}
+    for k, _ in Stats._fields_:
+        v = getattr(stats, k)
+        out[k] = list(v) if isinstance(v, C.Array) else v
+    return out
 
 
 _SIGS = {
@@ -410,7 +421,7 @@ class Solver:
         del keeps
         if rc not in (EIG_OK, EIG_ENOT_CONVERGED, EIG_EDUPLICATE):
             raise EigError(rc, "eig_solve")
-        st = {k: getattr(stats, k) for k, _ in Stats._fields_}
+        st = stats_dict(stats)
         if tr is not None:
             st["trace"] = tr[: stats.trace_rows].copy()
         return rc, st
@@ -544,7 +555,7 @@ def solve_batch(solvers, method="hybrid", X0s=None, opts=None, threads=0):
     rc = lib.eig_solve_batch(hs, cnt, METHODS[method] if isinstance(method, str) else int(method), arr,
                              1 if per else 0, int(threads), st, stats)
     del keeps
-    out = [{k: getattr(stats[i], k) for k, _ in Stats._fields_} for i in range(cnt)]
+    out = [stats_dict(stats[i]) for i in range(cnt)]
     return rc, [int(st[i]) for i in range(cnt)], out
 
 

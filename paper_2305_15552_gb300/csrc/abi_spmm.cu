@@ -80,8 +80,8 @@ eig_status eig_spmm_plan_info(const void* plan, eig_spmm_info* info) {
   info->layout = P->layout;
   const int64_t vb = (int64_t)eig::dtype_size(P->val_type);
   if (P->layout == EIG_LAYOUT_MIRRORED) {
-    info->layout_entries = P->m_slots;
-    info->device_bytes = P->m_slots * (1 + vb);
+    info->layout_entries = P->m_nblk * 256;
+    info->device_bytes = P->m_nblk * 256 * (2 + vb) + P->m_npan * 256;
   } else if (P->layout == EIG_LAYOUT_HALF) {
     info->layout_entries = P->tiled_entries;
     info->device_bytes = P->tiled_entries * (1 + vb) + P->tiled_rp * 2;

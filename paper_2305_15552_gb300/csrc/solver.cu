@@ -164,6 +164,23 @@ eig_status overlay_columns(const double* src, int ks, double* dst, int kd, int64
 // ---------------------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------------------
+static int spmm_shape_index(int nb, eig_dtype vt) {
+  int l = 0;
+  while ((1 << l) < nb && l < 5) ++l;
+  return 6 * (vt == EIG_F64 ? 1 : 0) + l;
+}
+
+void Ctx::count_spmm(int nb, eig_dtype vt, int64_t spmv_cols) {
+  const double bytes = h->plan.algorithmic_bytes(nb, dtype_size(vt));
+  const int k = spmm_shape_index(nb, vt);
+  s->spmm_calls += 1;
+  s->spmv_count += spmv_cols;
+  s->spmm_bytes += bytes;
+  s->spmm_calls_by_shape[k] += 1;
+  s->spmm_bytes_by_shape[k] += bytes;
+  if (o.timing) spmm_shape.push_back(k);
+}
+
 eig_status Ctx::spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (o.timing) {
@@ -176,9 +193,7 @@ eig_status Ctx::spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_
     EIG_CUDA_TRY(cudaEventRecord(b, st));
     spmm_ev.emplace_back(a, b);
   }
-  s->spmm_calls += 1;
-  s->spmv_count += spmv_cols;
-  s->spmm_bytes += h->plan.algorithmic_bytes(nb, dtype_size(vt));
+  count_spmm(nb, vt, spmv_cols);
   return EIG_OK;
 }
 
@@ -200,9 +215,7 @@ eig_status Ctx::spmm_cheb(const void* X, void* Y, int nb, eig_dtype vt, int64_t 
     EIG_CUDA_TRY(cudaEventRecord(b, st));
     spmm_ev.emplace_back(a, b);
   }
-  s->spmm_calls += 1;
-  s->spmv_count += spmv_cols;
-  s->spmm_bytes += h->plan.algorithmic_bytes(nb, dtype_size(vt));
+  count_spmm(nb, vt, spmv_cols);
   return EIG_OK;
 }
 
@@ -1324,9 +1337,10 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
       c.s->time_ms_rmm = ms;
     }
     double sum = 0.0;
-    for (auto& e : c.spmm_ev) {
-      cudaEventElapsedTime(&ms, e.first, e.second);
+    for (size_t i = 0; i < c.spmm_ev.size(); ++i) {
+      cudaEventElapsedTime(&ms, c.spmm_ev[i].first, c.spmm_ev[i].second);
       sum += ms;
+      c.s->spmm_ms_by_shape[c.spmm_shape[i]] += ms;
     }
     c.s->time_ms_spmm = sum;
     c.s->spmm_timed = (int64_t)c.spmm_ev.size();

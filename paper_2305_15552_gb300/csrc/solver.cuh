@@ -52,6 +52,8 @@ struct Ctx {
   eig_opts o;
   eig_stats* s;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
+  std::vector<int> spmm_shape;   // product shape of each timed call (index of eig_stats' by-shape arrays)
+  void count_spmm(int nb, eig_dtype vt, int64_t spmv_cols);
   eig_status spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols);
   // spmm with a fused Chebyshev step (spmm_run_cheb); EIG_EUNSUPPORTED leaves Y untouched
   eig_status spmm_cheb(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols, const void* Qp,

@@ -18,17 +18,6 @@ struct TileChunk {
 };
 static_assert(sizeof(TileChunk) == 32, "TileChunk layout");
 
-// One chunk of the mirrored layout: groups [g0, g1) of tile (row block, column block J), quads
-// [ent_off / 32, ent_off / 32 + nq) of the slot arrays.
-struct MirrorChunk {
-  int64_t ent_off;  // first slot (multiple of 32)
-  int32_t nq;       // quads in the chunk
-  int32_t J;
-  int32_t g0, g1;
-  int64_t pad;
-};
-static_assert(sizeof(MirrorChunk) == 32, "MirrorChunk layout");
-
 struct SpmmPlan {
   int64_t n = 0, nnz = 0;
   int R = 256, C = 64;                  // row block / column block sizes
@@ -63,16 +52,21 @@ struct SpmmPlan {
   DevBuf trp;                  // uint16 row offsets within chunks
   DevBuf err;                  // int: device-side error flags (bounded waits that gave up)
   DevBuf scratch;      // transposed partial products, n_slots * C * nb * sizeof(T)
-  // mirrored copy of H (both triangles; gather-only kernel): per row block, chunks of 8-row
-  // group quads (32 slots of uint8 column in tile + value), padded slots have column 0xFF
+  // mirrored copy of H (both triangles; gather-only kernel): per row block of 256 rows, its
+  // column tiles (64 columns) cut into panels of at most 24 tiles; per panel the rows ranked by
+  // entry count, lane l of warp w taking the row of rank 32 w + l; per (panel, warp) a stream
+  // of blocks of 32 lanes x 8 steps of (uint16 panel-local column, value), padded with
+  // zero-valued entries on zero rows
   bool mirrored = false;
-  int m_capq = 0;                    // quads per chunk at most
-  int64_t m_nchunks = 0, m_slots = 0, m_full_nnz = 0;
-  DevBuf m_chunk_ptr;                // int64[nRB+1]
-  DevBuf m_chunks;                   // MirrorChunk[m_nchunks]
-  DevBuf m_gq;                       // uint8[32 * m_nchunks]: quads of each group of a chunk
-  DevBuf m_col;                      // uint8[m_slots]
-  DevBuf m_val;                      // value type [m_slots]
+  int64_t m_npan = 0, m_nblk = 0, m_full_nnz = 0;
+  DevBuf m_rbp;                      // int32[nRB+1]: panels of row block I
+  DevBuf m_pt0, m_pnt;               // int32[m_npan]: first tile (into m_tcol) and tile count
+  DevBuf m_tcol;                     // int32: column block of each tile of the mirrored matrix
+  DevBuf m_perm;                     // uint8[m_npan * 256]: row (in its row block) of each slot
+  DevBuf m_steps;                    // int32[m_npan * 8]: steps of each (panel, warp)
+  DevBuf m_sboff;                    // int64[m_npan * 8 + 1]: first block of each (panel, warp)
+  DevBuf m_bcol;                     // uint16[m_nblk * 256]
+  DevBuf m_bval;                     // value type [m_nblk * 256]
   double algorithmic_bytes(int nb, size_t vec_bytes) const;
 };
 

@@ -1,28 +1,33 @@
-// Mirrored-tile SpMM: Y = H X with H = U + U_strict^T given by its stored upper triangle U
-// (Sec. 1; Eqs. upd1-upd2; half storage of Sec. 3.1 is the input format), GB300 layout.
+// Mirrored row-stream SpMM: Y = H X with H = U + U_strict^T given by its stored upper triangle U
+// (Sec. 1; Eqs. upd1-upd2; the half storage of Sec. 3.1 is the input format), GB300 layout.
 //
-// Why mirror.  In the half-stored kernels every stored h_ij feeds two products: a gather
-// y_i += h_ij x_j and a scatter z_j += h_ij x_i.  On sm_103a both run out of shared memory and
-// the scatter costs a read-modify-write of an nb-wide row per nonzero plus a reduction of the
-// warps' private partials; measured, that kernel is bound by the shared-memory pipe at ~4
-// wavefronts per nonzero while HBM idles.  Here the plan expands U once, on the device, into
-// both triangles, so the kernel only gathers: ~0.6 wavefronts per nonzero of H, at the price of
-// storing the strict lower triangle a second time (1-byte columns keep it to ~5 B per entry).
+// Why mirror.  In a half-stored kernel every stored h_ij feeds a gather y_i += h_ij x_j and a
+// scatter z_j += h_ij x_i; on sm_103a both run out of shared memory and the scatter costs a
+// read-modify-write of an nb-wide row per nonzero.  Here the plan expands U once, on the
+// device, into both triangles, so the kernel only gathers.
 //
-// Layout.  Row blocks of 256 rows (one CTA each), column blocks of 64 (a tile); inside a tile
-// the rows form 32 groups of 8.  A group's entries are stored as "quads": quad q of group g holds
-// step 4q..4q+3 of each of the group's 8 rows, as 32 (uint8 column in tile, value) slots ordered
-// [row][step]; rows shorter than the group's longest are padded with column 0xFF.  A chunk is
-// a run of consecutive groups of one tile (at most cap quads), with a 32-byte table of each
-// group's quad count; chunks of a row block are stored back to back, so a CTA streams them with
-// 1-D bulk copies (TMA) through a two-stage mbarrier pipeline.
-//
-// Kernel.  Lane (slot, q): the slot picks one (row, step-phase) of the warp's current group, q a
-// 16-byte slice of the nb-wide X row.  Each row's y stays in registers for the whole row block
-// and is written once.  X_J is staged per chunk and replicated across the 128-byte bank lines so
-// that the lanes of one shared-memory wavefront always read different copies: the gathers are
-// free of bank conflicts whatever the column indices.  The summation order is fixed (chunks,
-// quads, steps, then a fixed shuffle tree), so Y is bitwise reproducible.
+// What bounds it.  Every entry of H costs one gather of an nb-wide X row from shared memory
+// (64 bytes at nb = 16 in FP32), so at nb >= 16 the shared-memory pipe (128 bytes per clock
+// per SM), not HBM, is the limit; at nb <= 8 it is HBM.  The layout is built so that the pipe
+// moves little else and never stalls on bank conflicts, and so that HBM sees enough bytes in
+// flight:
+//   * one lane owns one row: per row block (256 rows, one CTA of 8 warps) and per panel of
+//     column tiles, the rows are ranked by their entry count and warp w's lane l takes the
+//     row of rank 32 w + l; the warp steps through its longest row's count, shorter rows
+//     padded with zero-valued entries (a few percent);
+//   * each step, lane l gathers its entry's whole X row in 16-byte pieces, starting at a
+//     lane-dependent piece, and the entries are ordered so that lane l reads a row of class
+//     (l + step) mod 8 (X row index mod 8): the 8 lanes of every shared-memory phase then hit
+//     distinct banks for any nb;
+//   * the entries (uint16 panel-local column + value) stream from HBM straight into registers,
+//     several 8-step blocks ahead, bypassing L1 and evicted first from L2; each lane loads
+//     only its own entries (16 + 32 bytes per block in FP32), so nothing is loaded twice;
+//   * X: the X rows of the row block's column tiles (64 rows each) are staged in shared
+//     memory by bulk copies (TMA) in panels of at most 24 tiles, evicted last from L2; a row
+//     block whose tiles do not fit takes several panels, its rows' partial sums added in Y
+//     in panel order.
+// Every sum runs in a fixed order (steps in stream order, panels in order): Y is bitwise
+// reproducible.
 #include <algorithm>
 #include <vector>
 
@@ -35,11 +40,15 @@ namespace eig {
 
 namespace {
 
-constexpr int kMR = 256;                 // rows per row block
-constexpr int kMC = 64;                  // columns per tile
-constexpr int kMG = 8;                   // rows per group
-constexpr int kMGroups = kMR / kMG;      // groups per tile
-constexpr unsigned kPadCol = 0xFFu;
+constexpr int kMR = 256;                 // rows per row block (one CTA)
+constexpr int kMC = 64;                  // columns per tile (unit of X staging)
+constexpr int kW = 8;                    // warps per CTA; warp w takes the rows of rank [32 w, 32 w + 32)
+constexpr int kRW = kMR / kW;            // rows per warp
+constexpr int kBS = 8;                   // steps per streamed block
+constexpr int kBE = 32 * kBS;            // entries per block (32 lanes)
+constexpr int kPT = 24;                  // tiles per panel at most
+constexpr int kPR = kPT * kMC;           // staged X rows per panel; 8 zero rows follow
+constexpr int kL2 = 6;                   // streamed blocks prefetched into L2 ahead of use
 
 // ---------------------------------------------------------------------------------------
 // Plan: both triangles as a CSR, built from U without sorting and without atomics on values
@@ -171,80 +180,146 @@ __global__ void k_mir_upper(int64_t n, const int64_t* __restrict__ rowptr, const
   }
 }
 
-// Thread per row of the mirrored CSR: entries of the row in each tile of its row block.
-__global__ void k_mir_rowtile_counts(int64_t n, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fcol,
-                                     const int64_t* __restrict__ tile_ptr, const int32_t* __restrict__ tile_col,
-                                     uint8_t* __restrict__ cnt) {
+// ---------------------------------------------------------------------------------------
+// Plan: the row streams
+// ---------------------------------------------------------------------------------------
+
+// Last column block of panel p (-1 for a panel without tiles).
+__device__ __forceinline__ int64_t panel_last_cb(const int32_t* __restrict__ pt0, const int32_t* __restrict__ pnt,
+                                                 const int32_t* __restrict__ tcol, int64_t p) {
+  return pnt[p] > 0 ? (int64_t)tcol[pt0[p] + pnt[p] - 1] : -1;
+}
+
+// Thread per row: entries the row has in each panel of its row block.
+__global__ void k_rs_counts(int64_t n, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fcol,
+                            const int32_t* __restrict__ rbp, const int32_t* __restrict__ pt0,
+                            const int32_t* __restrict__ pnt, const int32_t* __restrict__ tcol,
+                            uint16_t* __restrict__ cnt) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int64_t I = r / kMR;
-  const int rl = (int)(r - I * kMR);
-  int64_t t = tile_ptr[I];
-  const int64_t tend = tile_ptr[I + 1];
-  int run = 0;
-  int64_t tcur = -1;
-  for (int64_t k = fptr[r]; k < fptr[r + 1]; ++k) {
-    const int J = fcol[k] / kMC;
-    while (t < tend && tile_col[t] < J) ++t;
-    if (t != tcur) {
-      if (tcur >= 0) cnt[tcur * kMR + rl] = (uint8_t)run;
-      tcur = t;
-      run = 0;
+  const int lr = (int)(r - I * kMR);
+  int64_t k = fptr[r];
+  const int64_t kend = fptr[r + 1];
+  for (int64_t p = rbp[I]; p < rbp[I + 1]; ++p) {
+    const int64_t last = panel_last_cb(pt0, pnt, tcol, p);
+    int c = 0;
+    while (k < kend && (int64_t)(fcol[k] / kMC) <= last) {
+      ++k;
+      ++c;
     }
-    ++run;
+    cnt[p * kMR + lr] = (uint16_t)c;
   }
-  if (tcur >= 0) cnt[tcur * kMR + rl] = (uint8_t)run;
 }
 
-// Thread per (tile, group): quads of the group = ceil(longest row / 4).
-__global__ void k_mir_group_quads(int64_t n_tiles, const uint8_t* __restrict__ cnt, uint8_t* __restrict__ gq) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_tiles * kMGroups) return;
-  int m = 0;
+// CTA per panel: the panel's 256 rows ranked by entry count (descending, ties by row), so that
+// each warp's 32 lanes take rows of near-equal length; steps of each warp = its longest row.
+__global__ void __launch_bounds__(kMR) k_rs_rank(const uint16_t* __restrict__ cnt, uint8_t* __restrict__ perm,
+                                                 int32_t* __restrict__ steps) {
+  __shared__ uint16_t c[kMR];
+  const int64_t p = blockIdx.x;
+  const int t = threadIdx.x;
+  c[t] = cnt[p * kMR + t];
+  __syncthreads();
+  const int mine = c[t];
+  int rank = 0;
+  for (int u = 0; u < kMR; ++u) {
+    const int o = c[u];
+    rank += (o > mine) || (o == mine && u < t);
+  }
+  perm[p * kMR + rank] = (uint8_t)t;
+  if (rank % kRW == 0) steps[p * kW + rank / kRW] = mine;
+}
+
+// Every stream position starts as padding: value 0 and the zero row of the class its lane
+// wants at that step.  Block layout: [lane][step], 32 lanes x 8 steps.
+template <typename VS>
+__global__ void k_rs_pads(int64_t nent, uint16_t* __restrict__ bcol, VS* __restrict__ bval) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nent) return;
+  const int lane = (int)((e % kBE) / kBS), k = (int)(e % kBS);
+  bcol[e] = (uint16_t)(kPR + ((lane + k) & 7));
+  bval[e] = VS(0);
+}
+
+// Class (panel-local row mod 8) taken at a step whose lane wants class `want`: `want` while the
+// row has entries of it, else one that keeps its class mod 4, then mod 2.  Lane l wants
+// (l + step) mod 8, so the 8 lanes of a shared-memory phase read rows of 8 distinct classes.
+__device__ __forceinline__ int pick_class(int want, const int* left) {
+  const int order[8] = {0, 4, 2, 6, 1, 5, 3, 7};
 #pragma unroll
-  for (int k = 0; k < kMG; ++k) m = max(m, (int)cnt[i * kMG + k]);
-  gq[i] = (uint8_t)((m + 3) / 4);
+  for (int t = 0; t < 8; ++t) {
+    const int c = want ^ order[t];
+    if (left[c] > 0) return c;
+  }
+  return -1;
 }
 
-// Thread per row: scatter the row's entries of every tile into its group's quads.
+// Thread per (panel, slot): the slot's row's entries of the panel, class-ordered, into the
+// lane's column of the warp's stream.
 template <typename V>
-__global__ void k_mir_scatter(int64_t n, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fcol,
-                              const V* __restrict__ fval, const int64_t* __restrict__ tile_ptr,
-                              const int32_t* __restrict__ tile_col, const int64_t* __restrict__ gdst,
-                              uint8_t* __restrict__ mcol, V* __restrict__ mval) {
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const int64_t I = r / kMR;
-  const int rl = (int)(r - I * kMR);
-  const int g = rl / kMG, i = rl % kMG;
-  int64_t t = tile_ptr[I];
-  const int64_t tend = tile_ptr[I + 1];
-  int64_t tcur = -1, base = 0;
-  int kk = 0;
-  for (int64_t k = fptr[r]; k < fptr[r + 1]; ++k) {
-    const int c = fcol[k];
-    const int J = c / kMC;
-    while (t < tend && tile_col[t] < J) ++t;
-    if (t != tcur) {
-      tcur = t;
-      base = gdst[t * kMGroups + g];
-      kk = 0;
+__global__ void k_rs_scatter(int64_t npan, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fcol,
+                             const V* __restrict__ fval, int64_t n, const int32_t* __restrict__ pan_rb,
+                             const int32_t* __restrict__ pt0, const int32_t* __restrict__ pnt,
+                             const int32_t* __restrict__ tcol, const uint8_t* __restrict__ perm,
+                             const int64_t* __restrict__ sboff, uint16_t* __restrict__ bcol, V* __restrict__ bval) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npan * kMR) return;
+  const int64_t p = i / kMR;
+  const int slot = (int)(i % kMR), w = slot / kRW, lane = slot % kRW;
+  const int64_t r = (int64_t)pan_rb[p] * kMR + perm[i];
+  if (r >= n || pnt[p] == 0) return;
+  // the row's entries in this panel: columns in the panel's tile range
+  const int t0 = pt0[p], nt = pnt[p];
+  const int64_t first_cb = tcol[t0], last_cb = tcol[t0 + nt - 1];
+  int64_t e0 = fptr[r], e1 = fptr[r + 1];
+  {
+    int64_t lo = e0, hi = e1;
+    while (lo < hi) {
+      const int64_t m = (lo + hi) >> 1;
+      if ((int64_t)(fcol[m] / kMC) < first_cb) lo = m + 1; else hi = m;
     }
-    const int64_t slot = base + (int64_t)(kk >> 2) * 32 + i * 4 + (kk & 3);
-    mcol[slot] = (uint8_t)(c - J * kMC);
-    mval[slot] = fval[k];
-    ++kk;
+    e0 = lo;
+    hi = e1;
+    while (lo < hi) {
+      const int64_t m = (lo + hi) >> 1;
+      if ((int64_t)(fcol[m] / kMC) <= last_cb) lo = m + 1; else hi = m;
+    }
+    e1 = lo;
+  }
+  int left[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t cur[8];
+  for (int c = 0; c < 8; ++c) cur[c] = e0;
+  for (int64_t e = e0; e < e1; ++e) left[fcol[e] & 7]++;
+  const int64_t blk0 = sboff[p * kW + w];
+  const int64_t len = e1 - e0;
+  for (int64_t k = 0; k < len; ++k) {
+    const int c = pick_class((int)((lane + k) & 7), left);
+    int64_t e = cur[c];
+    while ((fcol[e] & 7) != c) ++e;
+    cur[c] = e + 1;
+    left[c]--;
+    const int32_t col = fcol[e];
+    const int32_t J = col / kMC;
+    int lo = 0, hi = nt - 1;  // position of J among the panel's tiles (ascending)
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (tcol[t0 + mid] < J) lo = mid + 1; else hi = mid;
+    }
+    const int64_t at = (blk0 + k / kBS) * kBE + lane * kBS + (k % kBS);
+    bcol[at] = (uint16_t)(lo * kMC + (col - J * kMC));
+    bval[at] = fval[e];
   }
 }
 
 template <typename V>
-eig_status mirror_fill(SpmmPlan* P, const int32_t* tile_rb, const int32_t* tile_cb, int64_t n_up_tiles,
-                       const int64_t* jt_ptr, const int32_t* jt_tile, int capq, cudaStream_t st) {
+eig_status rowstream_fill(SpmmPlan* P, const int32_t* tile_rb, const int32_t* tile_cb, int64_t n_up_tiles,
+                          const int64_t* jt_ptr, const int32_t* jt_tile, cudaStream_t st) {
   const int64_t n = P->n;
   const int tb = 256;
   const int64_t gb = (n + tb - 1) / tb;
   const V* val = static_cast<const V*>(P->val);
-  // 1. lower-part lengths and offsets
+  // 1. lower-part lengths and offsets of the mirrored CSR
   DevBuf cnt, off, lower, fptr;
   EIG_TRY(cnt.reserve(std::max<int64_t>(n_up_tiles, 1) * kMC * 4));
   EIG_TRY(off.reserve(std::max<int64_t>(n_up_tiles, 1) * kMC * 4));
@@ -282,259 +357,99 @@ eig_status mirror_fill(SpmmPlan* P, const int32_t* tile_rb, const int32_t* tile_
   cnt.release();
   off.release();
   lower.release();
-  // 3. tiles of the mirrored matrix and their group quad counts
+  // 3. tiles of the mirrored matrix per row block, cut into panels of at most kPT tiles
+  //    (balanced: a row block of t tiles takes ceil(t / kPT) panels of near-equal size; a row
+  //    block without tiles still gets one empty panel so that its rows are written)
   DevBuf ftile_ptr, ftile_col;
   std::vector<int64_t> h_tptr;
   std::vector<int32_t> h_tcol;
   EIG_TRY(build_tile_lists(n, kMR, kMC, fptr.as<int64_t>(), fcol.as<int32_t>(), st, ftile_ptr, ftile_col, h_tptr,
                            h_tcol));
   const int64_t nRB = (n + kMR - 1) / kMR;
-  const int64_t nt = h_tptr[nRB];
-  DevBuf rcnt, gq;
-  EIG_TRY(rcnt.reserve(std::max<int64_t>(nt, 1) * kMR));
-  EIG_TRY(gq.reserve(std::max<int64_t>(nt, 1) * kMGroups));
-  EIG_CUDA_TRY(cudaMemsetAsync(rcnt.p, 0, std::max<int64_t>(nt, 1) * kMR, st));
-  k_mir_rowtile_counts<<<(unsigned)gb, tb, 0, st>>>(n, fptr.as<int64_t>(), fcol.as<int32_t>(),
-                                                     ftile_ptr.as<int64_t>(), ftile_col.as<int32_t>(),
-                                                     rcnt.as<uint8_t>());
-  EIG_LAUNCH_CHECK("k_mir_rowtile_counts");
-  if (nt) {
-    k_mir_group_quads<<<(unsigned)((nt * kMGroups + tb - 1) / tb), tb, 0, st>>>(nt, rcnt.as<uint8_t>(),
-                                                                             gq.as<uint8_t>());
-    EIG_LAUNCH_CHECK("k_mir_group_quads");
-  }
-  std::vector<uint8_t> h_gq((size_t)nt * kMGroups);
-  if (nt) EIG_CUDA_TRY(cudaMemcpyAsync(h_gq.data(), gq.p, (size_t)nt * kMGroups, cudaMemcpyDeviceToHost, st));
-  EIG_CUDA_TRY(cudaStreamSynchronize(st));
-  rcnt.release();
-  gq.release();
-  // 4. chunks: runs of consecutive groups of one tile holding at most capq quads
-  std::vector<MirrorChunk> ch;
-  std::vector<uint8_t> cgq;
-  std::vector<int64_t> cptr(nRB + 1, 0);
-  std::vector<int64_t> gdst((size_t)nt * kMGroups, 0);
-  int64_t slots = 0;
+  std::vector<int32_t> rbp(nRB + 1, 0), pt0, pnt;
   for (int64_t I = 0; I < nRB; ++I) {
-    for (int64_t t = h_tptr[I]; t < h_tptr[I + 1]; ++t) {
-      const uint8_t* q = h_gq.data() + (size_t)t * kMGroups;
-      int g = 0;
-      while (g < kMGroups) {
-        MirrorChunk k;
-        k.ent_off = slots;
-        k.J = h_tcol[t];
-        k.g0 = g;
-        int nq = 0;
-        uint8_t tab[kMGroups] = {0};
-        while (g < kMGroups && (nq + q[g] <= capq || g == k.g0)) {
-          gdst[(size_t)t * kMGroups + g] = slots + (int64_t)nq * 32;
-          tab[g] = q[g];
-          nq += q[g];
-          ++g;
-        }
-        k.g1 = g;
-        k.nq = nq;
-        k.pad = 0;
-        if (nq == 0) continue;  // groups without entries (cannot end a tile with entries)
-        slots += (int64_t)nq * 32;
-        ch.push_back(k);
-        cgq.insert(cgq.end(), tab, tab + kMGroups);
-      }
+    const int64_t t0 = h_tptr[I], nt = h_tptr[I + 1] - t0;
+    const int64_t np = std::max<int64_t>(1, (nt + kPT - 1) / kPT);
+    int64_t t = t0;
+    for (int64_t q = 0; q < np; ++q) {
+      const int64_t sz = nt / np + (q < nt % np ? 1 : 0);
+      pt0.push_back((int32_t)t);
+      pnt.push_back((int32_t)sz);
+      t += sz;
     }
-    cptr[I + 1] = (int64_t)ch.size();
+    rbp[I + 1] = rbp[I] + (int32_t)np;
   }
-  P->m_nchunks = (int64_t)ch.size();
-  P->m_slots = slots;
-  P->m_capq = capq;
-  EIG_TRY(P->m_chunk_ptr.reserve((nRB + 1) * 8));
-  EIG_TRY(P->m_chunks.reserve(std::max<size_t>(ch.size(), 1) * sizeof(MirrorChunk)));
-  EIG_TRY(P->m_gq.reserve(std::max<size_t>(cgq.size(), 32)));
-  EIG_TRY(P->m_col.reserve(std::max<int64_t>(slots, 32)));
-  EIG_TRY(P->m_val.reserve(std::max<int64_t>(slots, 32) * sizeof(V)));
-  EIG_CUDA_TRY(cudaMemcpyAsync(P->m_chunk_ptr.p, cptr.data(), (nRB + 1) * 8, cudaMemcpyHostToDevice, st));
-  if (!ch.empty()) {
-    EIG_CUDA_TRY(cudaMemcpyAsync(P->m_chunks.p, ch.data(), ch.size() * sizeof(MirrorChunk), cudaMemcpyHostToDevice,
-                                 st));
-    EIG_CUDA_TRY(cudaMemcpyAsync(P->m_gq.p, cgq.data(), cgq.size(), cudaMemcpyHostToDevice, st));
-  }
-  EIG_CUDA_TRY(cudaMemsetAsync(P->m_col.p, (int)kPadCol, std::max<int64_t>(slots, 32), st));
-  EIG_CUDA_TRY(cudaMemsetAsync(P->m_val.p, 0, std::max<int64_t>(slots, 32) * sizeof(V), st));
-  DevBuf dgdst;
-  EIG_TRY(dgdst.reserve(std::max<size_t>(gdst.size(), 1) * 8));
-  if (!gdst.empty())
-    EIG_CUDA_TRY(cudaMemcpyAsync(dgdst.p, gdst.data(), gdst.size() * 8, cudaMemcpyHostToDevice, st));
-  k_mir_scatter<V><<<(unsigned)gb, tb, 0, st>>>(n, fptr.as<int64_t>(), fcol.as<int32_t>(), fval.as<V>(),
-                                                ftile_ptr.as<int64_t>(), ftile_col.as<int32_t>(),
-                                                dgdst.as<int64_t>(), P->m_col.as<uint8_t>(), P->m_val.as<V>());
-  EIG_LAUNCH_CHECK("k_mir_scatter");
-  EIG_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors and temporaries go out of scope
+  const int64_t npan = rbp[nRB];
+  P->m_npan = npan;
+  EIG_TRY(P->m_rbp.reserve((nRB + 1) * 4));
+  EIG_TRY(P->m_pt0.reserve(npan * 4));
+  EIG_TRY(P->m_pnt.reserve(npan * 4));
+  EIG_TRY(P->m_tcol.reserve(std::max<size_t>(h_tcol.size(), 1) * 4));
+  EIG_CUDA_TRY(cudaMemcpyAsync(P->m_rbp.p, rbp.data(), (nRB + 1) * 4, cudaMemcpyHostToDevice, st));
+  EIG_CUDA_TRY(cudaMemcpyAsync(P->m_pt0.p, pt0.data(), npan * 4, cudaMemcpyHostToDevice, st));
+  EIG_CUDA_TRY(cudaMemcpyAsync(P->m_pnt.p, pnt.data(), npan * 4, cudaMemcpyHostToDevice, st));
+  if (!h_tcol.empty())
+    EIG_CUDA_TRY(cudaMemcpyAsync(P->m_tcol.p, h_tcol.data(), h_tcol.size() * 4, cudaMemcpyHostToDevice, st));
+  ftile_ptr.release();
+  ftile_col.release();
+  // 4. entries per (panel, row); rows ranked per panel; steps per (panel, warp); stream offsets
+  std::vector<int32_t> pan_rb(npan);
+  for (int64_t I = 0; I < nRB; ++I)
+    for (int32_t q = rbp[I]; q < rbp[I + 1]; ++q) pan_rb[q] = (int32_t)I;
+  DevBuf d_pan_rb, cntp, steps;
+  EIG_TRY(d_pan_rb.reserve(npan * 4));
+  EIG_CUDA_TRY(cudaMemcpyAsync(d_pan_rb.p, pan_rb.data(), npan * 4, cudaMemcpyHostToDevice, st));
+  EIG_TRY(cntp.reserve(npan * kMR * 2));
+  EIG_CUDA_TRY(cudaMemsetAsync(cntp.p, 0, npan * kMR * 2, st));
+  k_rs_counts<<<(unsigned)gb, tb, 0, st>>>(n, fptr.as<int64_t>(), fcol.as<int32_t>(), P->m_rbp.as<int32_t>(),
+                                           P->m_pt0.as<int32_t>(), P->m_pnt.as<int32_t>(), P->m_tcol.as<int32_t>(),
+                                           cntp.as<uint16_t>());
+  EIG_LAUNCH_CHECK("k_rs_counts");
+  EIG_TRY(P->m_perm.reserve(npan * kMR));
+  EIG_TRY(steps.reserve(npan * kW * 4));
+  k_rs_rank<<<(unsigned)npan, kMR, 0, st>>>(cntp.as<uint16_t>(), P->m_perm.as<uint8_t>(), steps.as<int32_t>());
+  EIG_LAUNCH_CHECK("k_rs_rank");
+  std::vector<int32_t> h_steps(npan * kW);
+  std::vector<int64_t> sboff(npan * kW + 1, 0);
+  EIG_CUDA_TRY(cudaMemcpyAsync(h_steps.data(), steps.p, npan * kW * 4, cudaMemcpyDeviceToHost, st));
+  EIG_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < npan * kW; ++i) sboff[i + 1] = sboff[i] + (h_steps[i] + kBS - 1) / kBS;
+  const int64_t nblk = sboff[npan * kW];
+  P->m_nblk = nblk;
+  EIG_TRY(P->m_steps.reserve(npan * kW * 4));
+  EIG_CUDA_TRY(cudaMemcpyAsync(P->m_steps.p, steps.p, npan * kW * 4, cudaMemcpyDeviceToDevice, st));
+  EIG_TRY(P->m_sboff.reserve((npan * kW + 1) * 8));
+  EIG_CUDA_TRY(cudaMemcpyAsync(P->m_sboff.p, sboff.data(), (npan * kW + 1) * 8, cudaMemcpyHostToDevice, st));
+  // 5. the streams: padding everywhere, then each row's entries into its lane
+  const int64_t nent = std::max<int64_t>(nblk, 1) * kBE;
+  EIG_TRY(P->m_bcol.reserve(nent * 2));
+  EIG_TRY(P->m_bval.reserve(nent * sizeof(V)));
+  k_rs_pads<V><<<(unsigned)((nent + tb - 1) / tb), tb, 0, st>>>(nent, P->m_bcol.as<uint16_t>(), P->m_bval.as<V>());
+  EIG_LAUNCH_CHECK("k_rs_pads");
+  k_rs_scatter<V><<<(unsigned)((npan * kMR + tb - 1) / tb), tb, 0, st>>>(
+      npan, fptr.as<int64_t>(), fcol.as<int32_t>(), fval.as<V>(), n, d_pan_rb.as<int32_t>(), P->m_pt0.as<int32_t>(),
+      P->m_pnt.as<int32_t>(), P->m_tcol.as<int32_t>(), P->m_perm.as<uint8_t>(), P->m_sboff.as<int64_t>(),
+      P->m_bcol.as<uint16_t>(), P->m_bval.as<V>());
+  EIG_LAUNCH_CHECK("k_rs_scatter");
+  EIG_CUDA_TRY(cudaStreamSynchronize(st));  // temporaries go out of scope
   return EIG_OK;
 }
 
 // ---------------------------------------------------------------------------------------
 // Kernel
 // ---------------------------------------------------------------------------------------
-struct MirrorArgs {
+struct RsArgs {
   int64_t n;
-  int capq;
-  const int64_t* chunk_ptr;
-  const MirrorChunk* chunks;
-  const uint8_t* mcol;
-  const void* mval;
-  const uint8_t* mgq;
+  const int32_t* rbp;
+  const int32_t* pt0;
+  const int32_t* pnt;
+  const int32_t* tcol;
+  const uint8_t* perm;
+  const int32_t* steps;
+  const int64_t* sboff;
+  const uint16_t* bcol;
+  const void* bval;
   int* err;
-};
-
-__host__ __device__ constexpr size_t al128(size_t b) { return (b + 127) & ~size_t(127); }
-
-// Byte offsets inside one pipeline stage.
-struct MirrorStage {
-  size_t col, val, gq, xj, bytes;
-  __host__ __device__ MirrorStage(int capq, int vbytes, int rowbytes) {
-    col = 0;
-    val = al128((size_t)capq * 32);
-    gq = val + al128((size_t)capq * 32 * vbytes);
-    xj = gq + 128;
-    bytes = xj + al128((size_t)kMC * rowbytes);
-  }
-};
-
-// Four consecutive values of a quad row, widened to the arithmetic type.
-template <typename V, typename T> struct QuadLoad;
-template <typename T> struct QuadLoad<float, T> {
-  __device__ __forceinline__ static void ld(const float* p, T (&v)[4]) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    v[0] = (T)a.x; v[1] = (T)a.y; v[2] = (T)a.z; v[3] = (T)a.w;
-  }
-};
-template <typename T> struct QuadLoad<uint16_t, T> {
-  __device__ __forceinline__ static void ld(const uint16_t* p, T (&v)[4]) {
-    const uint2 a = *reinterpret_cast<const uint2*>(p);
-    v[0] = (T)__uint_as_float(a.x << 16);
-    v[1] = (T)__uint_as_float(a.x & 0xFFFF0000u);
-    v[2] = (T)__uint_as_float(a.y << 16);
-    v[3] = (T)__uint_as_float(a.y & 0xFFFF0000u);
-  }
-};
-template <typename T> struct QuadLoad<double, T> {
-  __device__ __forceinline__ static void ld(const double* p, T (&v)[4]) {
-    const double2 a = *reinterpret_cast<const double2*>(p);
-    const double2 b = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = (T)a.x; v[1] = (T)a.y; v[2] = (T)b.x; v[3] = (T)b.y;
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ T pick4(const T (&v)[4], int j) {
-  T r = v[0];
-  r = (j == 1) ? v[1] : r;
-  r = (j == 2) ? v[2] : r;
-  r = (j == 3) ? v[3] : r;
-  return r;
-}
-
-// Accumulation of y += v * x over one lane's EPL elements.
-//   Plain: X rows staged as T, fma in T.
-//   DF (FP64 vectors with FP32 or BF16 values): X rows staged as (hi, lo) FP32 pairs (same 8 bytes
-//   per element as FP64), each product taken exactly (hi part by an FMA-based two-product, lo part
-//   rounded) and summed in double-float (two-sum into hi, errors into lo): ~2^-44 relative per
-//   step, at FP32 instruction rate instead of the much slower FP64 pipe of sm_103a.
-template <bool DF, typename T, int EPL> struct MirrorAcc;
-template <typename T, int EPL> struct MirrorAcc<false, T, EPL> {
-  typedef T VT;   // value type in arithmetic
-  typedef Vec<T, EPL> XV;
-  Vec<T, EPL> y;
-  __device__ __forceinline__ void zero() { y.zero(); }
-  __device__ __forceinline__ static XV load(const unsigned char* p) {
-    return VecIO<T, EPL>::ld(reinterpret_cast<const T*>(p));
-  }
-  __device__ __forceinline__ void add(T v, const XV& x) {
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) y.v[e] = fma(v, x.v[e], y.v[e]);
-  }
-  __device__ __forceinline__ T get(int e) const { return y.v[e]; }
-  // staged form of one element
-  __device__ __forceinline__ static void stage(const T* src, unsigned char* dst) {
-    VecIO<T, EPL>::st(reinterpret_cast<T*>(dst), VecIO<T, EPL>::ld(src));
-  }
-  __device__ __forceinline__ static void stage_zero(unsigned char* dst) {
-    Vec<T, EPL> z;
-    z.zero();
-    VecIO<T, EPL>::st(reinterpret_cast<T*>(dst), z);
-  }
-};
-template <int EPL> struct MirrorAcc<true, double, EPL> {
-  typedef float VT;
-  struct XV { float h[EPL], l[EPL]; };
-  float hi[EPL], lo[EPL];
-  __device__ __forceinline__ void zero() {
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) hi[e] = lo[e] = 0.0f;
-  }
-  __device__ __forceinline__ static XV load(const unsigned char* p) {
-    XV x;
-    if (EPL == 2) {
-      const float4 a = *reinterpret_cast<const float4*>(p);
-      x.h[0] = a.x; x.l[0] = a.y; x.h[EPL - 1] = a.z; x.l[EPL - 1] = a.w;
-    } else {
-      const float2 a = *reinterpret_cast<const float2*>(p);
-      x.h[0] = a.x; x.l[0] = a.y;
-    }
-    return x;
-  }
-  __device__ __forceinline__ void add(float v, const XV& x) {
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-      const float p = v * x.h[e];
-      const float pe = fmaf(v, x.h[e], -p);          // v * x.h[e] = p + pe exactly
-      const float s = hi[e] + p;
-      const float bb = s - hi[e];
-      const float err = (hi[e] - (s - bb)) + (p - bb);  // hi + p = s + err exactly
-      hi[e] = s;
-      lo[e] = fmaf(v, x.l[e], lo[e] + (err + pe));
-    }
-  }
-  __device__ __forceinline__ double get(int e) const { return (double)hi[e] + (double)lo[e]; }
-  __device__ __forceinline__ static void stage(const double* src, unsigned char* dst) {
-    float* d = reinterpret_cast<float*>(dst);
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-      const double x = src[e];
-      const float h = __double2float_rn(x);
-      d[2 * e] = h;
-      d[2 * e + 1] = __double2float_rn(x - (double)h);
-    }
-  }
-  __device__ __forceinline__ static void stage_zero(unsigned char* dst) {
-    float* d = reinterpret_cast<float*>(dst);
-#pragma unroll
-    for (int e = 0; e < 2 * EPL; ++e) d[e] = 0.0f;
-  }
-};
-
-// Double-float accumulation applies to FP64 vectors with FP32 or BF16 values.
-template <typename T, typename V> struct MirrorDF { static constexpr bool value = false; };
-template <> struct MirrorDF<double, float> { static constexpr bool value = true; };
-template <> struct MirrorDF<double, uint16_t> { static constexpr bool value = true; };
-
-// Launch shape of the kernel for (T, NB).
-template <typename T, int NB> struct MirrorShape {
-  typedef LaneShape<T, NB> S;
-  static constexpr int EPL = S::EPL, L = S::L;
-  static constexpr int P = 32 / L;                    // slots per warp instruction
-  static constexpr int RPI = P < kMG ? P : kMG;       // rows of a group per instruction
-  static constexpr int SB = kMG / RPI;                // row sub-blocks of a group
-  static constexpr int M = P / RPI;                   // steps of a quad per instruction
-  static constexpr int JJ = 4 / M;                    // steps of a quad per lane
-  static constexpr int RB = NB * (int)sizeof(T);      // bytes of one X row
-  static constexpr int NCOPY = RB < 128 ? 128 / RB : 1;
-  static constexpr int LINE = RB < 128 ? 128 : RB;    // bytes of one replicated X row
-  // registers of y per lane with 4 warps (32-bit words); more warps when it is large
-  static constexpr int YREG4 = (kMGroups / 4) * SB * EPL * (int)sizeof(T) / 4;
-  // 4 warps for FP32 vectors (measured fastest); 8 for FP64-sized elements, whose
-  // double-float or FP64 arithmetic gains from more resident warps
-  static constexpr int WARPS = (sizeof(T) == 8 || YREG4 > 48) ? 8 : 4;
-  static constexpr int MINB = WARPS == 4 ? 2 : (YREG4 > 48 ? 2 : 3);   // resident CTAs aimed for
-  static constexpr int GPW = kMGroups / WARPS;
 };
 
 // Fused epilogue of a Chebyshev step (Alg. 3, Eq. chebypoly): Y = a (H X - c X) - Qp (first: no
@@ -547,193 +462,371 @@ struct MirrorEpi {
   int first;
 };
 
-template <typename T, typename V, int NB, bool CHEB = false>
-__global__ void __launch_bounds__(MirrorShape<T, NB>::WARPS * 32, MirrorShape<T, NB>::MINB)
-k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_bulk, MirrorEpi epi) {
-  typedef MirrorShape<T, NB> Sh;
-  constexpr int EPL = Sh::EPL, L = Sh::L, RPI = Sh::RPI, SB = Sh::SB, M = Sh::M, JJ = Sh::JJ;
-  constexpr int RB = Sh::RB, NCOPY = Sh::NCOPY, LINE = Sh::LINE, WARPS = Sh::WARPS, GPW = Sh::GPW;
-  constexpr int NT = WARPS * 32;
-  static_assert(M * JJ == 4, "quad split");
+// Double-float accumulation applies to FP64 vectors with FP32 or BF16 values.
+template <typename T, typename V> struct MirrorDF { static constexpr bool value = false; };
+template <> struct MirrorDF<double, float> { static constexpr bool value = true; };
+template <> struct MirrorDF<double, uint16_t> { static constexpr bool value = true; };
+
+// Lane geometry for (vector type T, value type V, kernel block width NB).
+//   ES: bytes of one staged X element (FP32; FP64; or a (hi, lo) FP32 pair for double-float);
+//   RBY: bytes of one staged X row, gathered by each lane as NCH pieces of LDB bytes.
+template <typename T, typename V, int NB> struct RsShape {
+  static constexpr bool DF = MirrorDF<T, V>::value;
+  static constexpr int ES = (int)sizeof(T);
+  static constexpr int RBY = NB * ES;
+  static constexpr int LDB = RBY >= 16 ? 16 : RBY;
+  static constexpr int NCH = RBY / LDB;       // pieces per row
+  static constexpr int EPC = LDB / ES;        // elements per piece
+  // lanes of a phase reading the same bank-line offset class get distinct pieces
+  static constexpr int ROTDIV = NCH >= 8 ? 1 : 8 / NCH;
+  static constexpr size_t XBYTES = (size_t)(kPR + 8) * RBY;
+  static constexpr int MINB0 = (int)(233472 / (XBYTES + 1024 + 128));
+  // register budget: up to 4 CTAs per SM for rows of <= 16 bytes, 3 for 32, else (and for
+  // FP64 values, whose blocks take twice the registers) 2
+  static constexpr int MAXB = sizeof(typename ValLoad<V>::storage) == 8 ? 2 : (RBY <= 16 ? 4 : (RBY <= 32 ? 3 : 2));
+  static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > MAXB ? MAXB : MINB0);   // resident CTAs per SM
+  // streamed blocks held in registers: the next block loads while the current one runs
+  static constexpr int PF = 2;
+  static constexpr int VW = (kBS * (int)sizeof(typename ValLoad<V>::storage)) / 4;   // value words per block
+};
+
+// Streamed loads: bypass L1, evict first from L2 (each entry is read once per product).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint4 ldg_stream(const void* p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+// Bulk prefetch of a global range into L2 (no registers, no shared memory).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_1d_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                 uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+// Shared-memory piece loads of 4, 8 or 16 bytes (raw words).
+template <int B> struct SLd;
+template <> struct SLd<4> {
+  __device__ __forceinline__ static void ld(uint32_t a, uint32_t* w) {
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w[0]) : "r"(a));
+  }
+};
+template <> struct SLd<8> {
+  __device__ __forceinline__ static void ld(uint32_t a, uint32_t* w) {
+    asm volatile("ld.shared.v2.b32 {%0,%1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "r"(a));
+  }
+};
+template <> struct SLd<16> {
+  __device__ __forceinline__ static void ld(uint32_t a, uint32_t* w) {
+    asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(a));
+  }
+};
+
+// y += v * x over a lane's N elements, x given as raw staged words.
+template <typename T, int N, bool DF> struct RsAcc;
+template <int N> struct RsAcc<float, N, false> {
+  typedef float VT;
+  typedef float OT;
+  static constexpr int N2 = (N + 1) / 2;
+  float2 y[N2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int e = 0; e < N2; ++e) y[e] = make_float2(0.0f, 0.0f);
+  }
+  __device__ __forceinline__ void add(int slot0, float v, const uint32_t* w, int nw) {
+    if (nw % 2 == 0) {
+      // packed FP32x2 multiply-add (sm_100+): two elements of y per instruction
+      const float2 vv = make_float2(v, v);
+#pragma unroll
+      for (int e = 0; e < nw; e += 2) {
+        const int s = (slot0 + e) / 2;
+        y[s] = __ffma2_rn(vv, make_float2(__uint_as_float(w[e]), __uint_as_float(w[e + 1])), y[s]);
+      }
+    } else {
+      y[slot0 / 2].x = fmaf(v, __uint_as_float(w[0]), y[slot0 / 2].x);
+    }
+  }
+  __device__ __forceinline__ OT get(int e) const { return (e & 1) ? y[e / 2].y : y[e / 2].x; }
+};
+template <int N> struct RsAcc<double, N, false> {
+  typedef double VT;
+  typedef double OT;
+  double y[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int e = 0; e < N; ++e) y[e] = 0.0;
+  }
+  __device__ __forceinline__ void add(int slot0, double v, const uint32_t* w, int nw) {
+#pragma unroll
+    for (int e = 0; e < nw / 2; ++e) y[slot0 + e] = fma(v, __hiloint2double(w[2 * e + 1], w[2 * e]), y[slot0 + e]);
+  }
+  __device__ __forceinline__ OT get(int e) const { return y[e]; }
+};
+// Double-float: X staged as (hi, lo) FP32 pairs (8 bytes per element, like FP64); each product
+// v * hi taken exactly (FMA two-product), summed into hi by two-sum, every error term and v * lo
+// into lo: ~2^-44 relative per step, at FP32 instruction rate.
+template <int N> struct RsAcc<double, N, true> {
+  typedef float VT;
+  typedef double OT;
+  float hi[N], lo[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int e = 0; e < N; ++e) hi[e] = lo[e] = 0.0f;
+  }
+  __device__ __forceinline__ void add(int slot0, float v, const uint32_t* w, int nw) {
+#pragma unroll
+    for (int e = 0; e < nw / 2; ++e) {
+      const int s = slot0 + e;
+      const float xh = __uint_as_float(w[2 * e]), xl = __uint_as_float(w[2 * e + 1]);
+      const float p = v * xh;
+      const float pe = fmaf(v, xh, -p);
+      const float t = hi[s] + p;
+      const float bb = t - hi[s];
+      const float err = (hi[s] - (t - bb)) + (p - bb);
+      hi[s] = t;
+      lo[s] = fmaf(v, xl, lo[s] + (err + pe));
+    }
+  }
+  __device__ __forceinline__ OT get(int e) const { return (double)hi[e] + (double)lo[e]; }
+};
+
+// Value k (0..7) of a lane's streamed block, widened to the arithmetic type.
+template <typename VS, typename VT> struct BlkVal;
+template <typename VT> struct BlkVal<float, VT> {
+  __device__ __forceinline__ static VT get(const uint32_t* w, int i) { return (VT)__uint_as_float(w[i]); }
+};
+template <typename VT> struct BlkVal<uint16_t, VT> {
+  __device__ __forceinline__ static VT get(const uint32_t* w, int i) {
+    const uint32_t u = w[i >> 1];
+    return (VT)__uint_as_float((i & 1) ? (u & 0xFFFF0000u) : (u << 16));
+  }
+};
+template <typename VT> struct BlkVal<double, VT> {
+  __device__ __forceinline__ static VT get(const uint32_t* w, int i) {
+    return (VT)__hiloint2double(w[2 * i + 1], w[2 * i]);
+  }
+};
+
+// One staged X element of type T (FP32, FP64; double-float pairs are staged from FP64).
+template <typename T, bool DF> struct Stage;
+template <> struct Stage<float, false> {
+  __device__ __forceinline__ static void put(unsigned char* d, float x) { *reinterpret_cast<float*>(d) = x; }
+};
+template <> struct Stage<double, false> {
+  __device__ __forceinline__ static void put(unsigned char* d, double x) { *reinterpret_cast<double*>(d) = x; }
+};
+template <> struct Stage<double, true> {
+  __device__ __forceinline__ static void put(unsigned char* d, double x) {
+    const float h = __double2float_rn(x);
+    reinterpret_cast<float*>(d)[0] = h;
+    reinterpret_cast<float*>(d)[1] = __double2float_rn(x - (double)h);
+  }
+};
+
+// Y (and X, Qp) rows have stride ld elements; this launch covers elements [col0, col0 + NB).
+template <typename T, typename V, int NB, bool CHEB>
+__global__ void __launch_bounds__(kW * 32, RsShape<T, V, NB>::MINB)
+k_spmm_mirror(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0, int xj_bulk, MirrorEpi epi) {
+  typedef RsShape<T, V, NB> Sh;
+  constexpr bool DF = Sh::DF;
+  constexpr int RBY = Sh::RBY, LDB = Sh::LDB, NCH = Sh::NCH, EPC = Sh::EPC, PF = Sh::PF, VW = Sh::VW;
+  constexpr int NW = LDB / 4;  // words per piece
   typedef typename ValLoad<V>::storage VS;
-  constexpr bool DF = MirrorDF<T, V>::value;
-  typedef MirrorAcc<DF, T, EPL> Acc;
-  typedef typename Acc::VT AT;
+  typedef RsAcc<T, NB, DF> Acc;
+  typedef typename Acc::VT VT;
+  typedef typename Acc::OT OT;
   extern __shared__ __align__(128) unsigned char smem[];
-  const MirrorStage SL(a.capq, (int)sizeof(VS), RB);
-  unsigned char* stage[2] = {smem, smem + SL.bytes};
-  unsigned char* dup = smem + 2 * SL.bytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(dup + (size_t)kMC * LINE);
+  unsigned char* xs = smem;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sh::XBYTES);
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t I = blockIdx.x;
   const int64_t r0 = I * kMR;
-  const int slot = lane / L, q = lane % L;
-  const int rsub = slot % RPI, sp = slot / RPI, cpy = slot % NCOPY;
-  const int64_t c0 = a.chunk_ptr[I], c1 = a.chunk_ptr[I + 1];
-  const VS* mval = static_cast<const VS*>(a.mval);
+  const int p0 = a.rbp[I], p1 = a.rbp[I + 1];
 
-  Acc y[GPW][SB];
-#pragma unroll
-  for (int gi = 0; gi < GPW; ++gi)
-#pragma unroll
-    for (int sb = 0; sb < SB; ++sb) y[gi][sb].zero();
-
+  // zero rows (one per class) for the padding entries; never overwritten by staging
+  for (int i = tid; i < 8 * RBY / 4; i += kW * 32) reinterpret_cast<uint32_t*>(xs + (size_t)kPR * RBY)[i] = 0u;
   if (tid == 0) {
     s_abort = 0;
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(bar, 1);
     mbar_init_fence();
   }
-  __syncthreads();
-
-  auto issue = [&](int64_t k, int s) {
-    const MirrorChunk ck = a.chunks[k];
-    const int64_t cb0 = (int64_t)ck.J * kMC;
-    const int64_t avail = min64(kMC, a.n - cb0);
-    const uint32_t cb = (uint32_t)ck.nq * 32u;
-    const uint32_t vb = cb * (uint32_t)sizeof(VS);
-    const uint32_t xb = xj_bulk ? (uint32_t)(avail * RB) : 0u;
-    mbar_arrive_expect_tx(&bar[s], cb + vb + 32u + xb);
-    unsigned char* st = stage[s];
-    tma_load_1d(st + SL.col, a.mcol + ck.ent_off, cb, &bar[s]);
-    tma_load_1d(st + SL.val, mval + ck.ent_off, vb, &bar[s]);
-    tma_load_1d(st + SL.gq, a.mgq + k * kMGroups, 32u, &bar[s]);
-    if (xj_bulk) tma_load_1d(st + SL.xj, X + cb0 * NB, xb, &bar[s]);
-  };
-  int issued[2] = {0, 0}, consumed[2] = {0, 0};  // meaningful in thread 0 only
-  if (tid == 0) {
-    if (c0 < c1) { issue(c0, 0); issued[0]++; }
-    if (c0 + 1 < c1) { issue(c0 + 1, 1); issued[1]++; }
-  }
-  // X rows are read from the replicated lines, or straight from the staged copy when one row
-  // already spans a whole bank line
-  constexpr bool kDup = NCOPY > 1 || DF;
-  int64_t prevJ = -1;
-  for (int64_t k = c0; k < c1; ++k) {
-    const int s = (int)((k - c0) & 1);
-    const uint32_t phase = (uint32_t)(((k - c0) >> 1) & 1);
-    const MirrorChunk ck = a.chunks[k];
-    const int64_t cb0 = (int64_t)ck.J * kMC;
-    const int64_t avail = min64(kMC, a.n - cb0);
-    unsigned char* st = stage[s];
-    if (!mbar_wait_bounded(&bar[s], phase)) {
-      atomicOr(a.err, 1);
-      s_abort = 1;
-    }
-    if (tid == 0) consumed[s]++;
-    __syncthreads();
-    if (s_abort) break;
-    const T* xsrc;
-    if (kDup || !xj_bulk) {
-      // replicate X_J (zero rows past n) unless this chunk continues the previous tile
-      if (ck.J != prevJ) {
-        const T* sxj = reinterpret_cast<const T*>(st + SL.xj);
-        for (int e = tid; e < kMC * NB / EPL; e += NT) {
-          const int c = (e * EPL) / NB, o = (e * EPL) % NB;
-          const T* src = xj_bulk ? sxj + c * NB + o : X + (cb0 + c) * NB + o;
+  // this lane's pieces start at piece `rot` of the row (distinct among the lanes of a phase
+  // whose rows share a bank-line offset)
+  const int rot = (lane / Sh::ROTDIV) % NCH;
+  uint32_t poff[NCH];
 #pragma unroll
-          for (int p = 0; p < NCOPY; ++p) {
-            unsigned char* dst = dup + (size_t)c * LINE + (size_t)p * RB + (size_t)o * sizeof(T);
-            if (c < avail) Acc::stage(src, dst);
-            else Acc::stage_zero(dst);
-          }
+  for (int j = 0; j < NCH; ++j) poff[j] = (uint32_t)(((j + rot) % NCH) * LDB);
+  const uint32_t xs_a = smem_u32(xs);
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  const uint16_t* bcol = a.bcol;
+  const VS* bval = static_cast<const VS*>(a.bval);
+  uint32_t xphase = 0;
+
+  for (int p = p0; p < p1; ++p) {
+    __syncthreads();  // the previous panel's gathers are done
+    const int t0 = a.pt0[p], npt = a.pnt[p];
+    if (xj_bulk) {
+      if (tid == 0 && npt > 0) {
+        uint32_t tot = 0;
+        for (int t = 0; t < npt; ++t) {
+          const int64_t cb0 = (int64_t)a.tcol[t0 + t] * kMC;
+          tot += (uint32_t)(min64(kMC, a.n - cb0) * RBY);
+        }
+        mbar_arrive_expect_tx(bar, tot);
+        for (int t = 0; t < npt; ++t) {
+          const int64_t cb0 = (int64_t)a.tcol[t0 + t] * kMC;
+          const uint32_t bytes = (uint32_t)(min64(kMC, a.n - cb0) * RBY);
+          tma_load_1d_hint(xs + (size_t)t * kMC * RBY, X + cb0 * NB, bytes, bar, pol_keep);
+        }
+      }
+      if (npt > 0) {
+        if (!mbar_wait_bounded(bar, xphase)) {
+          atomicOr(a.err, 1);
+          s_abort = 1;
         }
         __syncthreads();
+        if (s_abort) break;
+        xphase ^= 1u;
       }
-      xsrc = reinterpret_cast<const T*>(dup);
     } else {
-      // staged rows past n are never read: their columns do not occur
-      xsrc = reinterpret_cast<const T*>(st + SL.xj);
+      for (int64_t i = tid; i < (int64_t)npt * kMC * NB; i += kW * 32) {
+        const int t = (int)(i / (kMC * NB));
+        const int rr = (int)((i / NB) % kMC), e = (int)(i % NB);
+        const int64_t row = (int64_t)a.tcol[t0 + t] * kMC + rr;
+        if (row < a.n) Stage<T, DF>::put(xs + (size_t)(t * kMC + rr) * RBY + (size_t)e * Sh::ES, X[row * ld + col0 + e]);
+      }
+      __syncthreads();
     }
-    prevJ = ck.J;
-    const uint8_t* scol = st + SL.col;
-    const VS* sval = reinterpret_cast<const VS*>(st + SL.val);
-    // quad offsets of the chunk's groups: exclusive prefix of the 32 counts
-    const int gcount = st[SL.gq + lane];
-    int incl = gcount;
+
+    // this lane's row and the warp's stream
+    const int64_t r = r0 + a.perm[(int64_t)p * kMR + w * 32 + lane];
+    const int L = a.steps[(int64_t)p * kW + w];
+    const int64_t b0 = a.sboff[(int64_t)p * kW + w];
+    const int nb = (L + kBS - 1) / kBS;
+    Acc acc;
+    acc.zero();
+    uint4 bc[PF];
+    uint32_t bv[PF][VW];
+    auto load_blk = [&](int b, int s) {
+      const int64_t e = (b0 + b) * kBE + lane * kBS;
+      bc[s] = ldg_stream(bcol + e, pol_stream);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int excl = incl - gcount;
-    const unsigned char* xbase = reinterpret_cast<const unsigned char*>(xsrc) + (size_t)cpy * (kDup ? RB : 0) +
-                                 (size_t)q * EPL * sizeof(T);
+      for (int u = 0; u < VW; u += 4) {
+        const uint4 t = ldg_stream(reinterpret_cast<const unsigned char*>(bval + e) + u * 4, pol_stream);
+        bv[s][u] = t.x; bv[s][u + 1] = t.y; bv[s][u + 2] = t.z; bv[s][u + 3] = t.w;
+      }
+    };
+    // blocks kL2 ahead of the one running are prefetched into L2 by lane 0, so that the
+    // register loads one block ahead see L2 rather than HBM latency
+    auto prefetch_blk = [&](int b) {
+      if (lane == 0 && b < nb) {
+        prefetch_l2(bcol + (b0 + b) * kBE, kBE * 2);
+        prefetch_l2(bval + (b0 + b) * kBE, kBE * (uint32_t)sizeof(VS));
+      }
+    };
+    for (int b = 0; b < kL2; ++b) prefetch_blk(b);
 #pragma unroll
-    for (int gi = 0; gi < GPW; ++gi) {
-      const int g = gi * WARPS + w;
-      const int nq = __shfl_sync(0xffffffffu, gcount, g);
-      const int qo = __shfl_sync(0xffffffffu, excl, g);
+    for (int s = 0; s < PF; ++s)
+      if (s < nb) load_blk(s, s);
+    for (int b = 0; b < nb; b += PF) {
 #pragma unroll
-      for (int sb = 0; sb < SB; ++sb) {
-        const int i = rsub + sb * RPI;
-        for (int qq = 0; qq < nq; ++qq) {
-          const int base = (qo + qq) * 32 + i * 4;
-          const uint32_t cq = *reinterpret_cast<const uint32_t*>(scol + base);
-          AT vq[4];
-          QuadLoad<VS, AT>::ld(sval + base, vq);
+      for (int s = 0; s < PF; ++s) {
+        if (b + s < nb) {
+          prefetch_blk(b + s + kL2);
+          const uint32_t cw[4] = {bc[s].x, bc[s].y, bc[s].z, bc[s].w};
+          uint32_t vw[VW];
 #pragma unroll
-          for (int jj = 0; jj < JJ; ++jj) {
-            const int j = (M == 1) ? jj : sp + jj * M;
-            const unsigned c = (cq >> (8 * j)) & 0xFFu;
-            const AT v = (M == 1) ? vq[jj] : pick4(vq, j);
-            if (c != kPadCol) y[gi][sb].add(v, Acc::load(xbase + (size_t)c * LINE));
+          for (int u = 0; u < VW; ++u) vw[u] = bv[s][u];
+          if (b + s + PF < nb) load_blk(b + s + PF, s);
+          const int ks = min(kBS, L - (b + s) * kBS);   // steps in this block (warp-uniform)
+          auto step = [&](int k) {
+            const uint32_t c = (k & 1) ? (cw[k >> 1] >> 16) : (cw[k >> 1] & 0xFFFFu);
+            const VT v = BlkVal<VS, VT>::get(vw, k);
+            const uint32_t rowa = xs_a + c * (uint32_t)RBY;
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+              uint32_t xw[NW];
+              SLd<LDB>::ld(rowa + poff[j], xw);
+              acc.add(j * EPC, v, xw, NW);
+            }
+          };
+          if (ks == kBS) {
+            // a whole block: straight-line code, so the gathers of later steps can be issued
+            // ahead of the multiply-adds of earlier ones
+#pragma unroll
+            for (int k = 0; k < kBS; ++k) step(k);
+          } else {
+#pragma unroll
+            for (int k = 0; k < kBS; ++k)
+              if (k < ks) step(k);
           }
         }
       }
     }
-    __syncthreads();
-    if (tid == 0 && k + 2 < c1) {
-      fence_proxy_async();
-      issue(k + 2, s);
-      issued[s]++;
+    // the row's sum over this panel: stored (first panel) or added to the earlier panels'
+    if (r < a.n) {
+      const bool first_panel = (p == p0), last_panel = (p == p1 - 1);
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int jc0 = col0 + ((j + rot) % NCH) * EPC;   // first element of the piece
+        T* yp = Y + r * ld + jc0;
+        OT v[EPC];
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) v[e] = acc.get(j * EPC + e);
+        if (!first_panel) {
+          const Vec<T, EPC> old = VecIO<T, EPC>::ld(yp);
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) v[e] += (OT)old.v[e];
+        }
+        Vec<T, EPC> out;
+        if (CHEB && last_panel) {
+          const Vec<T, EPC> xv = VecIO<T, EPC>::ld(X + r * ld + jc0);
+          Vec<T, EPC> qv;
+          qv.zero();
+          if (!epi.first) qv = VecIO<T, EPC>::ld(static_cast<const T*>(epi.Qp) + r * ld + jc0);
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) {
+            if (!epi.active[jc0 + e]) {
+              out.v[e] = xv.v[e];
+            } else {
+              double yv = epi.a * ((double)(T)v[e] - epi.c * (double)xv.v[e]);
+              if (!epi.first) yv -= (double)qv.v[e];
+              out.v[e] = (T)yv;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) out.v[e] = (T)v[e];
+        }
+        VecIO<T, EPC>::st(yp, out);
+      }
     }
   }
   if (s_abort) {
-    // leave no bulk copy in flight into this CTA's shared memory (bounded waits)
-    if (tid == 0)
-      for (int ss = 0; ss < 2; ++ss)
-        while (consumed[ss] < issued[ss]) {
-          if (!mbar_wait_bounded(&bar[ss], (uint32_t)(consumed[ss] & 1))) break;
-          consumed[ss]++;
-        }
+    // leave no bulk copy in flight into this CTA's shared memory (bounded wait on the phase
+    // that gave up)
+    if (tid == 0) (void)mbar_wait_bounded(bar, xphase);
     __syncthreads();
-    return;
-  }
-  // combine the step phases of each row (fixed xor tree), then one store per row slice
-#pragma unroll
-  for (int gi = 0; gi < GPW; ++gi) {
-    const int g = gi * WARPS + w;
-#pragma unroll
-    for (int sb = 0; sb < SB; ++sb) {
-      Vec<T, EPL> out;
-#pragma unroll
-      for (int e = 0; e < EPL; ++e) {
-        T v = y[gi][sb].get(e);
-#pragma unroll
-        for (int o = RPI * L; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        out.v[e] = v;
-      }
-      const int64_t r = r0 + g * kMG + rsub + sb * RPI;
-      if (CHEB && sp == 0 && r < a.n) {
-        const T* Qp = static_cast<const T*>(epi.Qp);
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-          const int jc = q * EPL + e;
-          const T wv = X[r * NB + jc];
-          if (!epi.active[jc]) {
-            out.v[e] = wv;
-          } else {
-            double yv = epi.a * ((double)out.v[e] - epi.c * (double)wv);
-            if (!epi.first) yv -= (double)Qp[r * NB + jc];
-            out.v[e] = (T)yv;
-          }
-        }
-      }
-      if (sp == 0 && r < a.n) VecIO<T, EPL>::st(Y + r * NB + q * EPL, out);
-    }
   }
 }
 
@@ -743,10 +836,10 @@ k_spmm_mirror(MirrorArgs a, const T* __restrict__ X, T* __restrict__ Y, int xj_b
 // Host side
 // ---------------------------------------------------------------------------------------
 size_t mirror_bytes_estimate(const SpmmPlan* P) {
-  // mirrored CSR (temporary) + quads with ~1.5x padding
+  // mirrored CSR (temporary) + streams of 2-byte columns and values with ~5% padding
   const double fnnz = 2.0 * double(P->nnz);
   const double vb = double(dtype_size(P->val_type));
-  return (size_t)(fnnz * (4.0 + vb) + 1.6 * fnnz * (1.0 + vb) + 64.0 * double(P->n));
+  return (size_t)(fnnz * (4.0 + vb) + 1.1 * fnnz * (2.0 + vb) + 64.0 * double(P->n));
 }
 
 eig_status spmm_plan_build_mirror(SpmmPlan* P, const std::vector<int64_t>& h_tptr,
@@ -777,19 +870,16 @@ eig_status spmm_plan_build_mirror(SpmmPlan* P, const std::vector<int64_t>& h_tpt
   EIG_CUDA_TRY(cudaMemcpyAsync(d_tcb.p, tcb.data(), tcb.size() * 4, cudaMemcpyHostToDevice, st));
   EIG_CUDA_TRY(cudaMemcpyAsync(d_jptr.p, jptr.data(), jptr.size() * 8, cudaMemcpyHostToDevice, st));
   EIG_CUDA_TRY(cudaMemcpyAsync(d_jt.p, jt.data(), jt.size() * 4, cudaMemcpyHostToDevice, st));
-  // stage payload ~18 KB of quads
-  const int vb = (int)dtype_size(P->val_type);
-  const int capq = std::max(16, 18432 / (32 * (1 + vb)));
   eig_status s;
   if (P->val_type == EIG_F32)
-    s = mirror_fill<float>(P, d_trb.as<int32_t>(), d_tcb.as<int32_t>(), nt, d_jptr.as<int64_t>(), d_jt.as<int32_t>(),
-                           capq, st);
+    s = rowstream_fill<float>(P, d_trb.as<int32_t>(), d_tcb.as<int32_t>(), nt, d_jptr.as<int64_t>(),
+                              d_jt.as<int32_t>(), st);
   else if (P->val_type == EIG_F64)
-    s = mirror_fill<double>(P, d_trb.as<int32_t>(), d_tcb.as<int32_t>(), nt, d_jptr.as<int64_t>(),
-                            d_jt.as<int32_t>(), capq, st);
+    s = rowstream_fill<double>(P, d_trb.as<int32_t>(), d_tcb.as<int32_t>(), nt, d_jptr.as<int64_t>(),
+                               d_jt.as<int32_t>(), st);
   else
-    s = mirror_fill<uint16_t>(P, d_trb.as<int32_t>(), d_tcb.as<int32_t>(), nt, d_jptr.as<int64_t>(),
-                              d_jt.as<int32_t>(), capq, st);
+    s = rowstream_fill<uint16_t>(P, d_trb.as<int32_t>(), d_tcb.as<int32_t>(), nt, d_jptr.as<int64_t>(),
+                                 d_jt.as<int32_t>(), st);
   EIG_TRY(s);
   if (!P->err.p) {
     EIG_TRY(P->err.reserve(16));
@@ -800,36 +890,48 @@ eig_status spmm_plan_build_mirror(SpmmPlan* P, const std::vector<int64_t>& h_tpt
   return EIG_OK;
 }
 
-template <typename T, typename V, int NB>
-static size_t mirror_smem(const SpmmPlan* P) {
-  typedef MirrorShape<T, NB> Sh;
-  const MirrorStage SL(P->m_capq, (int)sizeof(typename ValLoad<V>::storage), Sh::RB);
-  return 2 * SL.bytes + (size_t)kMC * Sh::LINE + 2 * 8;
+// Kernel block width for (T, V, NB): NB itself while one panel of staged X rows fits in a
+// CTA's shared memory, else a column slice of it (the product then runs as several launches
+// over column slices, each reading the matrix once).
+template <typename T, typename V, int NB> struct RsSlice {
+  static constexpr int value =
+      (RsShape<T, V, NB>::XBYTES + 1024 <= 232448 || NB == 1) ? NB : RsSlice<T, V, NB / 2>::value;
+};
+template <typename T, typename V> struct RsSlice<T, V, 1> { static constexpr int value = 1; };
+
+template <typename T, typename V, int NBK, bool CHEB>
+static eig_status rs_launch(SpmmPlan* P, const T* X, T* Y, int ld, int col0, const MirrorEpi& epi, cudaStream_t st) {
+  typedef RsShape<T, V, NBK> Sh;
+  int dev = 0, maxsm = 0;
+  EIG_CUDA_TRY(cudaGetDevice(&dev));
+  EIG_CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t sm = Sh::XBYTES + 16;
+  if (sm > (size_t)maxsm) return EIG_EUNSUPPORTED;
+  RsArgs a;
+  a.n = P->n;
+  a.rbp = P->m_rbp.as<int32_t>();
+  a.pt0 = P->m_pt0.as<int32_t>();
+  a.pnt = P->m_pnt.as<int32_t>();
+  a.tcol = P->m_tcol.as<int32_t>();
+  a.perm = P->m_perm.as<uint8_t>();
+  a.steps = P->m_steps.as<int32_t>();
+  a.sboff = P->m_sboff.as<int64_t>();
+  a.bcol = P->m_bcol.as<uint16_t>();
+  a.bval = P->m_bval.p;
+  a.err = P->err.as<int>();
+  // X tiles by bulk copy: plain staging of whole, 16-byte aligned rows of a 16-byte multiple
+  const int xj_bulk = !Sh::DF && ld == NBK && (Sh::RBY % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
+  auto kern = k_spmm_mirror<T, V, NBK, CHEB>;
+  EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<(unsigned)P->nRB, kW * 32, sm, st>>>(a, X, Y, ld, col0, xj_bulk, epi);
+  EIG_LAUNCH_CHECK(CHEB ? "k_spmm_mirror_cheb" : "k_spmm_mirror");
+  return EIG_OK;
 }
 
 template <typename T, typename V, int NB>
 eig_status mirror_launch(SpmmPlan* P, const T* X, T* Y, cudaStream_t st) {
-  typedef MirrorShape<T, NB> Sh;
-  int dev = 0, maxsm = 0;
-  EIG_CUDA_TRY(cudaGetDevice(&dev));
-  EIG_CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t sm = mirror_smem<T, V, NB>(P);
-  if (sm > (size_t)maxsm) return EIG_EUNSUPPORTED;
-  MirrorArgs a;
-  a.n = P->n;
-  a.capq = P->m_capq;
-  a.chunk_ptr = P->m_chunk_ptr.as<int64_t>();
-  a.chunks = P->m_chunks.as<MirrorChunk>();
-  a.mcol = P->m_col.as<uint8_t>();
-  a.mval = P->m_val.p;
-  a.mgq = P->m_gq.as<uint8_t>();
-  a.err = P->err.as<int>();
-  // X_J by bulk copy needs 16-byte aligned rows of a 16-byte multiple
-  const int xj_bulk = (Sh::RB % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
-  auto kern = k_spmm_mirror<T, V, NB>;
-  EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  kern<<<(unsigned)P->nRB, Sh::WARPS * 32, sm, st>>>(a, X, Y, xj_bulk, MirrorEpi());
-  EIG_LAUNCH_CHECK("k_spmm_mirror");
+  constexpr int NBK = RsSlice<T, V, NB>::value;
+  for (int c0 = 0; c0 < NB; c0 += NBK) EIG_TRY((rs_launch<T, V, NBK, false>(P, X, Y, NB, c0, MirrorEpi(), st)));
   return EIG_OK;
 }
 
@@ -837,32 +939,14 @@ eig_status mirror_launch(SpmmPlan* P, const T* X, T* Y, cudaStream_t st) {
 template <typename T, typename V, int NB>
 eig_status mirror_launch_cheb(SpmmPlan* P, const T* X, T* Y, const T* Qp, const int* active, double alpha, double c,
                               int first, cudaStream_t st) {
-  typedef MirrorShape<T, NB> Sh;
-  int dev = 0, maxsm = 0;
-  EIG_CUDA_TRY(cudaGetDevice(&dev));
-  EIG_CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t sm = mirror_smem<T, V, NB>(P);
-  if (sm > (size_t)maxsm) return EIG_EUNSUPPORTED;
-  MirrorArgs a;
-  a.n = P->n;
-  a.capq = P->m_capq;
-  a.chunk_ptr = P->m_chunk_ptr.as<int64_t>();
-  a.chunks = P->m_chunks.as<MirrorChunk>();
-  a.mcol = P->m_col.as<uint8_t>();
-  a.mval = P->m_val.p;
-  a.mgq = P->m_gq.as<uint8_t>();
-  a.err = P->err.as<int>();
   MirrorEpi epi;
   epi.Qp = Qp;
   epi.active = active;
   epi.a = alpha;
   epi.c = c;
   epi.first = first;
-  const int xj_bulk = (Sh::RB % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
-  auto kern = k_spmm_mirror<T, V, NB, true>;
-  EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  kern<<<(unsigned)P->nRB, Sh::WARPS * 32, sm, st>>>(a, X, Y, xj_bulk, epi);
-  EIG_LAUNCH_CHECK("k_spmm_mirror_cheb");
+  constexpr int NBK = RsSlice<T, V, NB>::value;
+  for (int c0 = 0; c0 < NB; c0 += NBK) EIG_TRY((rs_launch<T, V, NBK, true>(P, X, Y, NB, c0, epi, st)));
   return EIG_OK;
 }
 

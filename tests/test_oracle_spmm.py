@@ -76,3 +76,16 @@ def test_planted_mistake_is_caught():
     wrong2 = U @ X + U.T @ X
     assert np.abs(wrong1 - A @ X).max() > 1e-3
     assert np.abs(wrong2 - A @ X).max() > 1e-3
+
+
+def test_parallel_upper_is_bitwise_the_same_product():
+    """The threaded product (row ranges of U and U^T in host threads) computes every output row
+    with the same sum in the same order: equal bit for bit to the single-threaded one."""
+    H = ci_matrix(3001, 120, 64, seed=5, storage="f64")
+    U = O.to_scipy_upper(H)
+    X = np.random.default_rng(3).standard_normal((H.n, 7))
+    for threads in (1, 3, 8):
+        P = O.parallel_upper(H, threads)
+        assert np.array_equal(O.sym_upper_matmul(H, X, P), O.sym_upper_matmul(H, X, U))
+        assert np.array_equal(O.sym_upper_matmul(H, X[:, 2], P), O.sym_upper_matmul(H, X[:, 2], U))
+        assert np.array_equal(P.diagonal(), U.diagonal())
