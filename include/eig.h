@@ -264,6 +264,13 @@ typedef struct {
                            /* 1e-13 for FP64)                                                       */
   const float* lp_params;  /* learned preconditioner (precond or rmm_precond = 2): host FP32 vector  */
                            /* of EIG_LP_PARAMS entries (layout at eig_lp_param_count); NULL = none */
+  double switch_gap;       /* hybrid (not in the paper): switch only once, in addition to the rule   */
+                           /* above, ||r_j|| <= switch_gap * gap_j for every wanted pair, gap_j the  */
+                           /* distance from theta_j to the front's nearest other Ritz value: by     */
+                           /* Davis-Kahan each Ritz vector is then within that angle of its          */
+                           /* eigenvector, where RMM-DIIS (which converges to the eigenvector        */
+                           /* nearest its start, Sec. 3.3) converges to the right one; 0 = off       */
+                           /* (default).  Ignored with switch_after.                                 */
 } eig_opts;
 
 typedef struct {

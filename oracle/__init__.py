@@ -29,7 +29,7 @@ from .block_lanczos import block_lanczos
 from .lobpcg import lobpcg
 from .chebfsi import chebfsi, lambda_ub_estimate, cheb_filter
 from .rmmdiis import rmmdiis, diis_coefficients, diis_extrapolate, rr2
-from .hybrid import hybrid, switch_tau
+from .hybrid import hybrid, switch_tau, gap_condition
 from .certify import true_relres, residual_bound, kato_temple, missed_eigenvalues
 
 __all__ = [n for n in dir() if not n.startswith("_")]

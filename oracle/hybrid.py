@@ -10,6 +10,12 @@ or a fixed number of front iterations has run (the sweeps of Tables 6-9).
 
 Reading: when theta_j^(k) is below 1e-12 in magnitude its term in tau uses the
 absolute change.
+
+Option not in the paper (switch_gap): the switch also waits until every wanted Ritz pair has
+||r_j|| <= switch_gap * gap_j, gap_j the distance to the block's nearest other Ritz value.  By
+the Davis-Kahan bound each Ritz vector is then within that angle of its eigenvector; RMM-DIIS,
+which has no orthogonalisation and converges to the eigenvector nearest its start (Sec. 3.3),
+then starts inside the right eigenvector's basin rather than between near-degenerate ones.
 """
 import numpy as np
 
@@ -28,9 +34,26 @@ def switch_tau(theta_k, theta_km1):
     return float(np.sqrt(np.sum(((tk - tp) / den) ** 2)) / tk.size)
 
 
+def gap_condition(theta, relres, nev, xi):
+    """True when ||r_j|| <= xi * gap_j for every wanted pair j < nev, gap_j the distance from
+    theta_j to the nearest other Ritz value of the block (Davis-Kahan: sin angle(z_j, v_j) <=
+    ||r_j|| / gap_j).  theta ascending, relres = ||r_j|| / |theta_j|."""
+    th = np.asarray(theta, dtype=np.float64)
+    rn = np.asarray(relres, dtype=np.float64) * np.abs(th)
+    for j in range(nev):
+        gap = np.inf
+        if j > 0:
+            gap = min(gap, th[j] - th[j - 1])
+        if j + 1 < th.size:
+            gap = min(gap, th[j + 1] - th[j])
+        if rn[j] > xi * gap:
+            return False
+    return True
+
+
 def hybrid(H, X0, nev, tol=1e-6, front="lobpcg", switch_res=None, switch_tau_tol=1e-7,
            switch_after=None, front_maxiter=200, rmm_maxiter=200, s_max=10, precond="jacobi", U=None,
-           rmm_precond="none"):
+           rmm_precond="none", switch_gap=None):
     U = to_scipy_upper(H) if U is None else U
     state = dict(prev=None, taus=[], why=None)
 
@@ -43,6 +66,8 @@ def hybrid(H, X0, nev, tol=1e-6, front="lobpcg", switch_res=None, switch_tau_tol
             if it >= switch_after:
                 state["why"] = "after"
                 return True
+            return False
+        if switch_gap is not None and not gap_condition(theta, relres, nev, switch_gap):
             return False
         if switch_res is not None and np.max(np.asarray(relres)[:nev]) <= switch_res:
             state["why"] = "res"

@@ -524,7 +524,7 @@ eig_status run_block_lanczos(Ctx& c, const double* X0, int x0c, int maxiter, con
     if (!qr_ok) { *reason = 4; break; }
     if (i + 1 >= maxblocks || it >= maxiter) break;
     if (stop) {
-      const int r = stop(it + 1, th.data(), rel.data());
+      const int r = stop(it + 1, th.data(), rel.data(), m);
       if (r) { *reason = r; break; }
     }
     // append R_{i+1} to T

@@ -526,7 +526,7 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
   *reason = 0;
   while (!conv && it < maxiter) {
     if (stop) {
-      const int r = stop(it, th.data(), rel.data());
+      const int r = stop(it, th.data(), rel.data(), nb);
       if (r) { *reason = r; break; }
     }
     ++it;
@@ -647,8 +647,9 @@ eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const 
 // RMM-DIIS stall rule: the worst relative residual of the wanted columns that are still
 // active has not halved within kRmmStall iterations (columns caught between near-degenerate
 // eigenvectors keep RMM-DIIS from converging, Sec. 3.3); the hybrid then hands over to LOBPCG.
-// Applied to the FP32-vector RMM-DIIS of the hybrid.
-constexpr int kRmmStall = 30;
+// Applied to the FP32-vector RMM-DIIS of the hybrid when its safety net is on (rmm_fallback);
+// without it RMM-DIIS runs to its iteration limit, as Alg. 4 does.
+constexpr int kRmmStall = 16;
 struct RmmStall {
   double best = INFINITY;
   int since = 0;
@@ -815,7 +816,7 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
     const double prev_sum = lp_on ? [&]() { double t = 0.0; for (int j = 0; j < nev; ++j) t += th[j]; return t; }()
                                   : 0.0;
     done = refresh();
-    if (!done && stall.update(rel, act, nev)) {
+    if (!done && c.o.rmm_fallback && stall.update(rel, act, nev)) {
       c.trace(1, it, th.data(), rel.data(), nev);
       break;
     }
@@ -1122,7 +1123,7 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
   auto front_then_rmm = [&](eig_method front) -> eig_status {
     std::vector<double> prev;
     double best_rel = INFINITY;
-    auto stop = [&](int it, const double* th, const double* rel) -> int {
+    auto stop = [&](int it, const double* th, const double* rel, int count) -> int {
       double mxr = 0.0;
       for (int j = 0; j < nev; ++j) mxr = std::max(mxr, rel[j]);
       // the front has become unstable (Sec. 2.8: LOBPCG near convergence): residuals climbing
@@ -1142,6 +1143,18 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
       }
       prev.assign(th, th + nev);
       if (c.o.switch_after > 0) return it >= c.o.switch_after ? 3 : 0;
+      // gap condition (option switch_gap): every wanted Ritz vector is within angle switch_gap of
+      // an eigenvector (Davis-Kahan: sin angle <= ||r_j|| / gap_j, gap_j the distance from theta_j
+      // to the block's other Ritz values), so that RMM-DIIS, which converges to the eigenvector
+      // nearest its start, starts inside the right one's basin
+      if (c.o.switch_gap > 0.0) {
+        for (int j = 0; j < nev; ++j) {
+          double gap = INFINITY;
+          if (j > 0) gap = std::min(gap, th[j] - th[j - 1]);
+          if (j + 1 < count) gap = std::min(gap, th[j + 1] - th[j]);
+          if (rel[j] * std::fabs(th[j]) > c.o.switch_gap * gap) return 0;
+        }
+      }
       if (c.o.switch_res > 0.0) {
         double mx = 0.0;
         for (int j = 0; j < nev; ++j) mx = std::max(mx, rel[j]);
@@ -1188,7 +1201,10 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
       theta.resize(nev);
       return EIG_OK;
     }
-    Xf.release();
+    // the front's own Ritz vectors beyond the n_ev wanted ones (its guard columns) are kept for
+    // the safety net's start block
+    const bool have_guards = front == EIG_LOBPCG && nb > nev;
+    if (!have_guards) Xf.release();
     int rit = 0;
     EIG_TRY(run_rmmdiis(c, Xs.as<double>(), c.o.rmm_maxiter > 0 ? c.o.rmm_maxiter : c.o.maxiter, &rit, &conv,
                         &theta));
@@ -1215,18 +1231,36 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
       DevBuf Xf2, X0f;
       EIG_TRY(Xf2.reserve((size_t)n * nb * 8));
       EIG_TRY(X0f.reserve((size_t)n * nev * 8));
-      // start from the RMM-DIIS vectors without the ones that repeat another (LOBPCG fills the
-      // block up with seeded random columns)
+      // start from the RMM-DIIS vectors without the ones that repeat another, followed by the
+      // front's guard Ritz vectors n_ev .. n_b - 1 (LOBPCG front; otherwise LOBPCG fills the block
+      // up with seeded random columns)
       std::vector<int> keep;
       EIG_TRY(independent_columns(c, h->Xres.as<double>(), nev, nev, 0.5, &keep));
       if (keep.empty()) keep.push_back(0);
+      const int kk = (int)keep.size();
+      const int ng = have_guards ? nb - nev : 0;
+      EIG_TRY(X0f.reserve((size_t)n * (kk + ng) * 8));
       ColIdx ci;
-      for (int q = 0; q < 32; ++q) ci.c[q] = q < (int)keep.size() ? keep[q] : 0;
-      k_gather_columns<<<num_sms() * 8, 256, 0, c.st>>>(h->Xres.as<double>(), nev, ci, (int)keep.size(),
-                                                        X0f.as<double>(), n);
+      for (int q = 0; q < 32; ++q) ci.c[q] = q < kk ? keep[q] : 0;
+      DevBuf Xk, Xg;
+      EIG_TRY(Xk.reserve((size_t)n * kk * 8));
+      k_gather_columns<<<num_sms() * 8, 256, 0, c.st>>>(h->Xres.as<double>(), nev, ci, kk, Xk.as<double>(), n);
       EIG_LAUNCH_CHECK("k_gather_columns");
-      const eig_status fr = run_lobpcg(c, X0f.as<double>(), (int)keep.size(), c.o.maxiter, StopFn(), &fit,
-                                       &freason, &fc, Xf2.as<double>(), &theta);
+      if (ng > 0) {
+        ColIdx cg;
+        for (int q = 0; q < 32; ++q) cg.c[q] = q < ng ? nev + q : 0;
+        EIG_TRY(Xg.reserve((size_t)n * ng * 8));
+        k_gather_columns<<<num_sms() * 8, 256, 0, c.st>>>(Xf.as<double>(), nb, cg, ng, Xg.as<double>(), n);
+        EIG_LAUNCH_CHECK("k_gather_columns");
+      }
+      // X0f = [Xk | Xg] (row-major n x (kk + ng))
+      EIG_CUDA_TRY(cudaMemcpy2DAsync(X0f.p, (size_t)(kk + ng) * 8, Xk.p, (size_t)kk * 8, (size_t)kk * 8, n,
+                                     cudaMemcpyDeviceToDevice, c.st));
+      if (ng > 0)
+        EIG_CUDA_TRY(cudaMemcpy2DAsync(X0f.as<double>() + kk, (size_t)(kk + ng) * 8, Xg.p, (size_t)ng * 8,
+                                       (size_t)ng * 8, n, cudaMemcpyDeviceToDevice, c.st));
+      const eig_status fr = run_lobpcg(c, X0f.as<double>(), kk + ng, c.o.maxiter, StopFn(), &fit, &freason, &fc,
+                                       Xf2.as<double>(), &theta);
       c.o.vec_type = vt_saved;
       c.o.precond = pre_saved;
       EIG_TRY(fr);

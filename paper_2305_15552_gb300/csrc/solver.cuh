@@ -78,9 +78,9 @@ struct Ctx {
   ~Ctx();
 };
 
-// Stop rule of a front method: called after every iteration with the Ritz values and relative
-// residuals of the leading n_ev pairs; returns a switch reason (> 0) to stop.
-typedef std::function<int(int it, const double* theta, const double* relres)> StopFn;
+// Stop rule of a front method: called after every iteration with the ascending Ritz values and
+// relative residuals of the leading `count` (>= n_ev) pairs; returns a switch reason (> 0) to stop.
+typedef std::function<int(int it, const double* theta, const double* relres, int count)> StopFn;
 
 eig_status run_lobpcg(Ctx& c, const double* X0, int x0_cols, int maxiter, const StopFn& stop, int* iters,
                       int* reason, bool* converged, double* X64_out, std::vector<double>* theta_out);

@@ -255,8 +255,8 @@ __device__ __forceinline__ int pick_class(int want, const int* left) {
   return -1;
 }
 
-// Thread per (panel, slot): the slot's row's entries of the panel, class-ordered, into the
-// lane's column of the warp's stream.
+// Thread per (panel, slot): the slot's row's entries of the panel, class-ordered (the diagonal
+// entry last), into the lane's column of the warp's stream.
 template <typename V>
 __global__ void k_rs_scatter(int64_t npan, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fcol,
                              const V* __restrict__ fval, int64_t n, const int32_t* __restrict__ pan_rb,
@@ -287,18 +287,29 @@ __global__ void k_rs_scatter(int64_t npan, const int64_t* __restrict__ fptr, con
     }
     e1 = lo;
   }
+  // the diagonal entry, if it lies in this panel, takes the row's last step: the small
+  // off-diagonal terms are summed before the (typically much larger) diagonal one is added
+  int64_t ediag = -1;
+  for (int64_t e = e0; e < e1; ++e)
+    if ((int64_t)fcol[e] == r) ediag = e;
   int left[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int64_t cur[8];
   for (int c = 0; c < 8; ++c) cur[c] = e0;
-  for (int64_t e = e0; e < e1; ++e) left[fcol[e] & 7]++;
+  for (int64_t e = e0; e < e1; ++e)
+    if (e != ediag) left[fcol[e] & 7]++;
   const int64_t blk0 = sboff[p * kW + w];
   const int64_t len = e1 - e0;
   for (int64_t k = 0; k < len; ++k) {
-    const int c = pick_class((int)((lane + k) & 7), left);
-    int64_t e = cur[c];
-    while ((fcol[e] & 7) != c) ++e;
-    cur[c] = e + 1;
-    left[c]--;
+    int64_t e;
+    if (ediag >= 0 && k == len - 1) {
+      e = ediag;
+    } else {
+      const int c = pick_class((int)((lane + k) & 7), left);
+      e = cur[c];
+      while ((fcol[e] & 7) != c || e == ediag) ++e;
+      cur[c] = e + 1;
+      left[c]--;
+    }
     const int32_t col = fcol[e];
     const int32_t J = col / kMC;
     int lo = 0, hi = nt - 1;  // position of J among the panel's tiles (ascending)

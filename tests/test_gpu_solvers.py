@@ -65,13 +65,17 @@ def test_lobpcg_fp64_random_start_laplacian():
 
 @pytest.mark.parametrize("vt", ["f32", "f64"])
 def test_hybrid_lobpcg_rmmdiis(H3000f, vt):
+    """The paper's hybrid as printed: LOBPCG until tau <= 1e-7 (Eq. switchtau), then
+    unpreconditioned RMM-DIIS (Alg. 4) with no safety net, to 1e-6; the oracle's own hybrid on
+    this matrix converges the same way (tests/test_oracle_cheb_rmm.py)."""
     H, lam = H3000f
     S = Solver(H, 5, 8)
-    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type=vt, trace_cap=1000)
+    rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type=vt, trace_cap=1000, rmm_fallback=0, rmm_maxiter=500)
     tr = st.pop("trace")
     msg = f"{st}\n" + "\n".join(" ".join(f"{v:.3e}" for v in row) for row in tr)
     assert rc == 0, msg
     assert st["iterations_rmm"] > 0 and st["switch_reason"] == 1, msg
+    assert st["iterations_fallback"] == 0, msg          # RMM-DIIS itself met the tolerance
     th, _, _ = S.ritz()
     assert np.allclose(th, lam[:5], rtol=1e-6), msg
     check_result(H, S, lam[:5])
@@ -82,6 +86,7 @@ def test_hybrid_nev8_nb16(H3000f):
     S = Solver(H, 8, 16)
     rc, st = S.solve("hybrid", X0=guess(H, 16), vec_type="f32")
     assert rc == 0, st
+    assert st["iterations_rmm"] > 0 and st["iterations_fallback"] == 0, st
     check_result(H, S, lam[:8])
 
 
@@ -95,16 +100,38 @@ def test_rmmdiis_from_close_guess(H3000):
     check_result(H, S, lam[:5])
 
 
-def test_lobpcg_c1_size_fp64():
-    """n = 20,000, ~100 nnz/row, 64-tiles, FP64 (the plain FP64 LOBPCG configuration)."""
+@pytest.fixture(scope="module")
+def c1():
+    """n = 20,000, ~100 nnz/row, 64-tiles, FP64 (the plain FP64 LOBPCG / Lanczos configuration):
+    the matrix, its small-space start, and the oracle's LOBPCG from that start to 1e-10."""
     H = ci_matrix(20000, 100, 64, seed=1, storage="f64")
     X0 = guess(H, 8, 2000)
-    ref = O.lobpcg(H, X0, 5, tol=1e-10, maxiter=300)
+    U = O.to_scipy_upper(H)
+    ref = O.lobpcg(H, X0, 5, tol=1e-10, maxiter=300, U=U)
     assert ref.converged
+    return H, X0, U, ref
+
+
+def test_lobpcg_c1_size_fp64(c1):
+    H, X0, U, ref = c1
     S = Solver(H, 5, 8)
     rc, st = S.solve("lobpcg", X0=X0, vec_type="f64")
     assert rc == 0, st
-    check_result(H, S, ref.theta[:5])
+    th, _ = check_result(H, S, ref.theta[:5])
+    assert O.missed_eigenvalues(H, th, 5, U=U).size == 0
+
+
+def test_lanczos_c1_size_fp64(c1):
+    """Lanczos with full reorthogonalisation (Sec. 2.1) at n = 20,000 in FP64, started from the
+    mean of the small-space vectors: the oracle's eigenvalues to 1e-6 relative, true residuals
+    <= 1e-6, and Lanczos from three random starts (the oracle's missed-eigenvalue guard) finds no
+    wanted eigenvalue the result lacks."""
+    H, X0, U, ref = c1
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("lanczos", X0=X0, vec_type="f64")
+    assert rc == 0, st
+    th, _ = check_result(H, S, ref.theta[:5])
+    assert O.missed_eigenvalues(H, th, 5, U=U).size == 0
 
 
 def test_invalid_arguments():
@@ -148,6 +175,7 @@ def test_hybrid_block_lanczos_front(H3000):
     S = Solver(H, 5, 8)
     rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type="f64", front="block_lanczos", switch_tau=1e-7)
     assert rc == 0, st
+    assert st["iterations_fallback"] == 0, st
     check_result(H, S, lam[:5])
 
 
@@ -171,6 +199,7 @@ def test_hybrid_preconditioned_rmmdiis(H3000f, vt):
     S = Solver(H, 5, 8)
     rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type=vt, rmm_precond=1)
     assert rc == 0, st
+    assert st["iterations_rmm"] > 0 and st["iterations_fallback"] == 0, st
     check_result(H, S, lam[:5])
 
 
@@ -251,4 +280,23 @@ def test_hybrid_bf16_values(vt):
     S = Solver(H, 5, 8)
     rc, st = S.solve("hybrid", X0=guess(H, 8), vec_type=vt, rmm_precond=1)
     assert rc == 0, st
+    assert st["iterations_fallback"] == 0, st
     check_result(H, S, lam[:5])
+
+
+def test_hybrid_gap_switch_matches_oracle():
+    """The gap condition on the switch (switch_gap, not in the paper): the GPU hybrid (FP32 vectors,
+    Jacobi-preconditioned RMM-DIIS) and the oracle's hybrid with the same rule both converge to
+    the dense spectrum's lowest eight, the GPU without its safety net, and switch at the same
+    front iteration up to one (the Ritz values differ in rounding)."""
+    H = ci_matrix(3000, 100, 64, seed=1, storage="f32")
+    lam, _ = O.lowest_eigpairs(O.to_dense(H), 8)
+    X0 = guess(H, 16)
+    ref = O.hybrid(H, X0, 8, tol=1e-6, switch_res=1e-2, switch_tau_tol=None, switch_gap=0.03, rmm_maxiter=300,
+                   rmm_precond="jacobi")
+    assert ref.converged
+    S = Solver(H, 8, 16)
+    rc, st = S.solve("hybrid", X0=X0, vec_type="f32", switch_res=1e-2, switch_tau=0.0, switch_gap=0.03, rmm_precond=1)
+    assert rc == 0 and st["iterations_fallback"] == 0, st
+    assert abs(st["iterations_front"] - ref.extra["front"].iterations) <= 1, (st, ref.extra["front"].iterations)
+    check_result(H, S, lam)

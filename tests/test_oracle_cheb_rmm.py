@@ -98,6 +98,34 @@ def test_switch_tau_hand_value():
     assert O.switch_tau([3.0, 4.0], [3.0, 4.0]) == 0.0
 
 
+def test_gap_condition_hand_values():
+    """||r_j|| <= xi * gap_j by hand: theta = (1.0, 1.1, 2.0), relres = (1e-3, 1e-2, 1e-3):
+    ||r|| = (1e-3, 1.1e-2, 2e-3), gaps (0.1, 0.1, 0.9).  With xi = 0.2 pair 1 needs 1.1e-2 <= 0.02:
+    true; with xi = 0.1, 1.1e-2 <= 0.01 fails.  Only the wanted pairs count (nev = 1 passes at
+    xi = 0.02: 1e-3 <= 0.002)."""
+    th, rel = [1.0, 1.1, 2.0], [1e-3, 1e-2, 1e-3]
+    assert O.gap_condition(th, rel, 3, 0.2)
+    assert not O.gap_condition(th, rel, 3, 0.1)
+    assert O.gap_condition(th, rel, 1, 0.02)
+    assert not O.gap_condition(th, rel, 1, 0.009)
+
+
+def test_hybrid_gap_switch_converges_on_the_cut_shell():
+    """With the gap condition (not in the paper) the oracle's hybrid switches once the wanted
+    Ritz vectors are separated from their neighbours and its RMM-DIIS converges to the dense
+    spectrum's lowest pairs."""
+    H = ci_matrix(3000, 100, 64, seed=1, storage="f64")
+    lam, _ = O.lowest_eigpairs(O.to_dense(H), 8)
+    X0 = pad_rows(O.lowest_eigpairs(O.to_dense(principal_submatrix(H, 300)), 16)[1], H.n)
+    r = O.hybrid(H, X0, 8, tol=1e-6, switch_res=1e-2, switch_tau_tol=None, switch_gap=0.03, rmm_maxiter=200,
+                 rmm_precond="jacobi")
+    assert r.converged
+    np.testing.assert_allclose(np.sort(r.theta), lam, rtol=1e-9)
+    fr = r.extra["front"]
+    last = fr.history[-1]
+    assert O.gap_condition(last["theta"], last["relres"], 8, 0.03) or r.extra["rmm"] is None
+
+
 def test_hybrid_ci_vs_dense():
     H = ci_matrix(3000, 100, 64, seed=1, storage="f64")
     lam, _ = O.lowest_eigpairs(O.to_dense(H), 5)
