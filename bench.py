@@ -831,7 +831,8 @@ def run_sweep(args, ws, rank, local):
     """Switch-point sweep of the hybrid (Sec. 4, its fixed-switch tables and the optimal-vs-tau
     tables of Sec. 4.1) on a paper-shaped synthetic matrix: n = --sweep-n (197,822, the size of
     the 6Li N_max = 6 problem of Table 2), ~--sweep-nnz-per-row (1080) nonzeros per full row (the
-    density of the paper's matrices), block pattern 256, FP32 values and vectors.  For n_ev = 5
+    density of the paper's matrices), block pattern 256, FP32 values and FP64 vectors (the paper's
+    precision).  For n_ev = 5
     (n_b = 8) and n_ev = 10 (n_b = 16), and for both fronts (LOBPCG, block Lanczos): the front
     alone to 1e-6, RMM-DIIS switched in after 5 / 10 / 15 / 20 front iterations, at tau <= 1e-4 and
     tau <= 1e-7 (Eq. switchtau), and every switch point 1..--sweep-max-switch, whose fewest SpMVs
@@ -856,7 +857,7 @@ def run_sweep(args, ws, rank, local):
             a2 = argparse.Namespace(**{**vars(args), "nev": nev, "nb": nb})
             X0 = torch.tensor(initial_guess(H, a2, binding), device="cuda")
             S = binding.Solver(H, nev, nb)
-            base = dict(vec_type="f32", tol=args.tol, maxiter=500, rmm_maxiter=500, rmm_fallback=0, rmm_precond=0,
+            base = dict(vec_type="f64", tol=args.tol, maxiter=500, rmm_maxiter=500, rmm_fallback=0, rmm_precond=0,
                         s_max=args.s_max, switch_res=0.0)
 
             def run(method, **o):

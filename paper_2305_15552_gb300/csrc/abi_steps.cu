@@ -36,7 +36,7 @@ __global__ void k_small_matmul(const double* __restrict__ A, const double* __res
 eig_status cholqr2_impl2(void* X, void* X2, int64_t n, int k, eig_dtype vt, double* R, cudaStream_t st) {
   AsyncScratch sc(st);
   const size_t gb = gram_scratch_bytes(1, k);
-  EIG_TRY(sc.get(gb + 5 * (size_t)k * k * 8 + 256 * 4));
+  EIG_TRY(sc.get(gb + 4 * (size_t)k * k * 8 + small_chol_inv_work_bytes(k) + 256 * 4));
   unsigned char* base = (unsigned char*)sc.p;
   double* part = (double*)base;
   double* G = (double*)(base + gb);
@@ -44,7 +44,7 @@ eig_status cholqr2_impl2(void* X, void* X2, int64_t n, int k, eig_dtype vt, doub
   double* Ri = R1 + k * k;
   double* R2 = Ri + k * k;
   double* work = R2 + k * k;
-  int* info = (int*)(work + k * k);
+  int* info = (int*)((unsigned char*)work + small_chol_inv_work_bytes(k));
   int hinfo = 0;
   for (int pass = 0; pass < 2; ++pass) {
     BlockList bl;

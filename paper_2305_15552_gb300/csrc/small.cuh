@@ -1,4 +1,4 @@
-// Small dense FP64 kernels (projected problems of the Rayleigh-Ritz procedure, Cholesky of
+// Small dense kernels, FP64 in and out, double-float inside (projected problems of the Rayleigh-Ritz procedure, Cholesky of
 // Gram matrices, DIIS least squares, 2x2 pencils).  Internal interface.
 #pragma once
 #include "common.cuh"
@@ -38,7 +38,8 @@ eig_status small_rr(const double* A, const double* G, int k, int nb, double piv_
 
 // CholQR factor: G = R^T R (upper R) and Rinv = R^{-1}, k x k; info = SMALL_BREAKDOWN when a
 // squared pivot falls below piv_tol * max diag(G).  Rinv32: optional float copy.
-// work: k*k doubles of device scratch.
+// work: small_chol_inv_work_bytes(k) bytes of device scratch.
+size_t small_chol_inv_work_bytes(int k);
 eig_status small_chol_inv(const double* G, int k, double piv_tol, double* R, double* Rinv, float* Rinv32,
                           void* work, int* info, cudaStream_t st);
 
