@@ -25,6 +25,15 @@ void set_cuda_error(cudaError_t e, const char* what, const char* file, int line)
     }                                                                        \
   } while (0)
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` and never lowers it.  The
+// attribute is per function and process-wide, so host threads that launch the same kernel
+// with different sizes (the instances of a batch) must not undercut each other's launches.
+cudaError_t ensure_dyn_smem(const void* kern, size_t bytes);
+template <typename K>
+inline cudaError_t ensure_dyn_smem(K* kern, size_t bytes) {
+  return ensure_dyn_smem(reinterpret_cast<const void*>(kern), bytes);
+}
+
 // Count of kernel launches made by this library (every launch site checks through here).
 void count_launch();
 

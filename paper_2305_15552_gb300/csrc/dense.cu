@@ -199,7 +199,7 @@ static eig_status gram_launch(const BlockList& blocks, const PairList& pl, int n
                       : (ntiles <= 2 * kGramThreads ? k_gram<T, TM, 2, true> : k_gram<T, TM, 4, true>))
                    : ((ntiles <= kGramThreads) ? k_gram<T, TM, 1, false>
                       : (ntiles <= 2 * kGramThreads ? k_gram<T, TM, 2, false> : k_gram<T, TM, 4, false>));
-  if (sm > 48 * 1024) EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  if (sm > 48 * 1024) EIG_CUDA_TRY(::eig::ensure_dyn_smem(kern, (int)sm));
   kern<<<g, kGramThreads, sm, st>>>(blocks, pl, nb, n, rpc, static_cast<double*>(part));
   EIG_LAUNCH_CHECK("k_gram");
   return reduce_partials(static_cast<double*>(part), g, pl.n * nb * nb, G, st);
@@ -263,11 +263,11 @@ eig_status block_apply(const BlockList& in, int nb, const double* M, int m, void
   const int grid = num_sms() * 8;
   if (vt == EIG_F32) {
     const size_t sm = (size_t)in.n * nb * m * 4;
-    if (sm > 48 * 1024) EIG_CUDA_TRY(cudaFuncSetAttribute(k_block_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (sm > 48 * 1024) EIG_CUDA_TRY(::eig::ensure_dyn_smem(k_block_apply<float>, (int)sm));
     k_block_apply<float><<<grid, 256, sm, st>>>(in, nb, M, m, static_cast<float*>(Out), beta, n);
   } else if (vt == EIG_F64) {
     const size_t sm = (size_t)in.n * nb * m * 8;
-    if (sm > 48 * 1024) EIG_CUDA_TRY(cudaFuncSetAttribute(k_block_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (sm > 48 * 1024) EIG_CUDA_TRY(::eig::ensure_dyn_smem(k_block_apply<double>, (int)sm));
     k_block_apply<double><<<grid, 256, sm, st>>>(in, nb, M, m, static_cast<double*>(Out), beta, n);
   } else {
     return EIG_EINVAL;

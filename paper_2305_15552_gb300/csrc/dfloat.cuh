@@ -4,8 +4,8 @@
 // a divide ~420), so the small sequential dense solves run on the FP32 units in this format.
 // The error-free transformations are the textbook ones (Knuth's two-sum, the FMA two-product;
 // Dekker 1971, Bailey's double-double library; additions in the cheap form with a normwise
-// bound); division and square root start from the FP32 approximate reciprocal / root and
-// correct it against the double-float residual.
+// bound); division and the reciprocal square root start from the FP32 approximate reciprocal /
+// root and correct it once against the double-float residual (one Newton step).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -59,15 +59,14 @@ __device__ __forceinline__ dfl dfma(dfl a, dfl b, dfl acc) {
   return quick_two_sum(s.hi, s.lo + (acc.lo + e));
 }
 __device__ __forceinline__ double dfma(double a, double b, double acc) { return fma(a, b, acc); }
-// Quotient from an approximate FP32 reciprocal, corrected twice against the exact residual.
+// Quotient from an approximate FP32 reciprocal rb (~2^-23): q1 = a rb, then one correction
+// q2 from the residual a - b q1 (~2^-23 a, computed to double-float accuracy) brings the
+// relative error to ~2^-46.
 __device__ __forceinline__ dfl operator/(dfl a, dfl b) {
   const float rb = rcp_approx(b.hi);
   const float q1 = a.hi * rb;
   const dfl r = a - b * dfl(q1, 0.0f);
-  const float q2 = r.hi * rb;
-  const dfl r2 = r - b * dfl(q2, 0.0f);
-  const float q3 = r2.hi * rb;
-  return dfl(q1, 0.0f) + (quick_two_sum(q2, q3));
+  return quick_two_sum(q1, r.hi * rb);
 }
 __device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 __device__ __forceinline__ dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
@@ -89,17 +88,24 @@ __device__ __forceinline__ dfl copysign(dfl mag, dfl sgn) {
   return (sgn.hi < 0.0f || (sgn.hi == 0.0f && signbit(sgn.hi))) ? -m : m;
 }
 __device__ __forceinline__ bool isfinite(dfl a) { return ::isfinite(a.hi) && ::isfinite(a.lo); }
-// Newton correction of the FP32 root: s + (a - s^2) / (2 s)
+// 1 / sqrt(a): the FP32 approximate root y (~2^-22) corrected once by Newton's step for
+// f(y) = 1/y^2 - a, y' = y + y (1 - a y^2) / 2, with a y^2 formed to double-float accuracy
+// (the correction is ~2^-22 y, so FP32 suffices for it): relative error ~2^-44.
+__device__ __forceinline__ dfl rsqrt(dfl a) {
+  if (!(a.hi > 0.0f)) return dfl(0.0f, 0.0f);
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.hi));
+  const float y2 = y * y;
+  const dfl yy(y2, fmaf(y, y, -y2));                      // y^2 exactly
+  const dfl h = a * yy;
+  const float r = (1.0f - h.hi) - h.lo;                  // 1 - a y^2, small
+  return quick_two_sum(y, 0.5f * y * r);
+}
+// sqrt(a) = a / sqrt(a)
 __device__ __forceinline__ dfl sqrt(dfl a) {
   if (!(a.hi > 0.0f)) return dfl(0.0f, 0.0f);
-  float s;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(a.hi));
-  const dfl e = a - dfl(s, 0.0f) * dfl(s, 0.0f);
-  const dfl s1 = quick_two_sum(s, e.hi * rcp_approx(2.0f * s));
-  const dfl e1 = a - s1 * s1;   // second correction: the approximate root is only ~22 bits
-  return s1 + dfl(e1.hi * rcp_approx(2.0f * s1.hi), 0.0f);
+  return a * rsqrt(a);
 }
-__device__ __forceinline__ dfl rsqrt(dfl a) { return dfl(1.0f, 0.0f) / sqrt(a); }
 
 // 1 when negative (the sign of the leading part), else 0
 __device__ __forceinline__ int sign_bit(dfl a) { return (int)(__float_as_uint(a.hi) >> 31); }

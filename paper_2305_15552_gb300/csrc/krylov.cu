@@ -346,10 +346,10 @@ eig_status run_lanczos(Ctx& c, const double* X0, int x0c, int* iters, bool* conv
   if (m == nev) {
     const size_t sm = (size_t)k * m * 8;
     if (L.vt == EIG_F32) {
-      EIG_CUDA_TRY(cudaFuncSetAttribute(k_basis_combine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+      EIG_CUDA_TRY(::eig::ensure_dyn_smem(k_basis_combine<float>, 160 * 1024));
       k_basis_combine<float><<<num_sms() * 4, 256, sm, c.st>>>((const float*)L.V, k, L.Z, m, h->n, h->Xres.as<double>());
     } else {
-      EIG_CUDA_TRY(cudaFuncSetAttribute(k_basis_combine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+      EIG_CUDA_TRY(::eig::ensure_dyn_smem(k_basis_combine<double>, 160 * 1024));
       k_basis_combine<double><<<num_sms() * 4, 256, sm, c.st>>>((const double*)L.V, k, L.Z, m, h->n, h->Xres.as<double>());
     }
     EIG_LAUNCH_CHECK("k_basis_combine");

@@ -480,7 +480,7 @@ eig_status lp_grad(const float* params, const float* F, const float* r, const fl
   const int grid = grad_grid();
   const size_t smem = kGradSmemFloats * sizeof(float);
   // set on every call: the attribute belongs to the current device
-  EIG_CUDA_TRY(cudaFuncSetAttribute(k_lp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  EIG_CUDA_TRY(::eig::ensure_dyn_smem(k_lp_grad, (int)smem));
   k_lp_grad<<<grid, kGradThreads, smem, st>>>(params, F, r, z, colw, n, m, (double*)workspace);
   EIG_LAUNCH_CHECK("k_lp_grad");
   return reduce_partials((const double*)workspace, grid, kGradOut, out, st);

@@ -376,11 +376,11 @@ eig_status rmm_update(const double* xt, const double* hxt, const void* rt, const
   const int grid = rmm_grid(n, mp);
   const size_t sm = (size_t)kRmmThreads * (1 + win_after.s) * 8;
   if (vt == EIG_F32) {
-    EIG_CUDA_TRY(cudaFuncSetAttribute(k_rmm_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    EIG_CUDA_TRY(::eig::ensure_dyn_smem(k_rmm_update<float>, (int)sm));
     k_rmm_update<float><<<grid, kRmmThreads, sm, st>>>(xt, hxt, (const float*)rt, (const float*)hrt, g, theta,
                                                         slot_new, win_after, mp, n, xh, (float*)rh, thh, part);
   } else {
-    EIG_CUDA_TRY(cudaFuncSetAttribute(k_rmm_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    EIG_CUDA_TRY(::eig::ensure_dyn_smem(k_rmm_update<double>, (int)sm));
     k_rmm_update<double><<<grid, kRmmThreads, sm, st>>>(xt, hxt, (const double*)rt, (const double*)hrt, g, theta,
                                                          slot_new, win_after, mp, n, xh, (double*)rh, thh, part);
   }

@@ -249,41 +249,41 @@ __device__ __forceinline__ int sturm_count(const R* __restrict__ d, const R* __r
 // a pivot below tiny is raised to tiny (inverse iteration's near-singular shift).  Factor
 // entry i sits at [i * s] (several vectors' factors interleaved).
 template <typename R>
+__device__ __forceinline__ R guard_tiny(R v, R tiny) {
+  return (fabs(v) < tiny) ? copysign(tiny, v == R(0.0) ? R(1.0) : v) : v;
+}
+
+template <typename R>
 __device__ __forceinline__ void tri_shift_factor(const R* __restrict__ d, const R* __restrict__ e, int k, R sigma,
                                                  R tiny, R* __restrict__ u0, R* __restrict__ u1,
                                                  R* __restrict__ u2, R* __restrict__ lm,
                                                  unsigned char* __restrict__ piv, int s) {
-  R c0 = d[0] - sigma;                   // running pivot row: (c0, c1, c2) in columns i, i+1, i+2
+  R c0 = d[0] - sigma;                   // running pivot row: (c0, c1, 0) in columns i, i+1, i+2
   R c1 = (k > 1) ? e[0] : R(0.0);
-  R c2 = 0.0;
   for (int i = 0; i + 1 < k; ++i) {
     const R sub = e[i];
     const R nd = d[i + 1] - sigma;
     const R ne = (i + 2 < k) ? e[i + 1] : R(0.0);
     if (fabs(c0) >= fabs(sub)) {
-      const R l = sub / ((c0 == R(0.0)) ? tiny : c0);
-      u0[i * s] = c0; u1[i * s] = c1; u2[i * s] = c2;
+      const R rc = R(1.0) / guard_tiny(c0, tiny);
+      const R l = sub * rc;
+      u0[i * s] = rc; u1[i * s] = c1; u2[i * s] = R(0.0);
       lm[i * s] = l;
       piv[i * s] = 0;
       c0 = dfma(-l, c1, nd);
       c1 = ne;
-      c2 = 0.0;
     } else {
-      const R l = c0 / sub;
-      u0[i * s] = sub; u1[i * s] = nd; u2[i * s] = ne;
+      const R rs = R(1.0) / guard_tiny(sub, tiny);
+      const R l = c0 * rs;
+      u0[i * s] = rs; u1[i * s] = nd; u2[i * s] = ne;
       lm[i * s] = l;
       piv[i * s] = 1;
-      c0 = dfma(-l, nd, c1);
-      c1 = dfma(-l, ne, c2);
-      c2 = 0.0;
+      const R t = c1;
+      c0 = dfma(-l, nd, t);
+      c1 = -l * ne;
     }
   }
-  u0[(k - 1) * s] = c0;
-  for (int i = 0; i < k; ++i) {
-    R v = u0[i * s];
-    if (fabs(v) < tiny) v = copysign(tiny, v == R(0.0) ? R(1.0) : v);
-    u0[i * s] = R(1.0) / v;
-  }
+  u0[(k - 1) * s] = R(1.0) / guard_tiny(c0, tiny);
 }
 
 // y <- (T - sigma I)^{-1} y from the factors of tri_shift_factor.
@@ -597,25 +597,57 @@ __device__ void tri_eig_lowest(int k, int m, TriWork<R> W, double* w, R* red) {
 }
 
 // Z (k x m row-major) = Q Y with Q = H_0 H_1 ... H_{k-3}; Y column t at Y + t*ldy.  One
-// half-warp per vector: each reflector costs a 16-lane dot product and an update.
+// half-warp per vector, reflectors in pairs: with a = v_j . y, b = v_{j-1} . y and
+// c_j = v_{j-1} . v_j, H_{j-1} H_j y = y - 2 a v_j - 2 (b - 2 a c_j) v_{j-1}, so the two dot
+// products of a pair reduce together.  cv: k scalars of scratch for the c_j.
 template <typename R, typename ZT>
-__device__ void back_transform(int k, int m, const R* V, R* Y, int ldy, ZT* Z) {
+__device__ void back_transform(int k, int m, const R* V, R* Y, int ldy, ZT* Z, R* cv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 1 + warp; j <= k - 3; j += nw) {
+    R s = 0.0;
+    for (int i = j + 1 + lane; i < k; i += 32) s = dfma(V[(size_t)(j - 1) * k + i], V[(size_t)j * k + i], s);
+    s = wsum(s);
+    if (lane == 0) cv[j] = s;
+  }
+  __syncthreads();
   const int hl = threadIdx.x & 15, hw = threadIdx.x >> 4, nh = blockDim.x >> 4;
   const int tmax = ((m + nh - 1) / nh) * nh;   // uniform trip count: whole warps shuffle
   for (int t0 = 0; t0 < tmax; t0 += nh) {
     const int t = t0 + hw;
     const bool act = t < m;
     R* y = Y + (size_t)(act ? t : 0) * ldy;
-    for (int j = k - 3; j >= 0; --j) {
-      const R* v = V + (size_t)j * k;
+    int j = k - 3;
+    for (; j >= 1; j -= 2) {
+      const R* va = V + (size_t)j * k;         // applied first
+      const R* vb = V + (size_t)(j - 1) * k;
+      R da = 0.0, db = 0.0;
+      if (act)
+        for (int i = j + hl; i < k; i += 16) {
+          const R yi = y[i];
+          da = dfma(va[i], yi, da);
+          db = dfma(vb[i], yi, db);
+        }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        da = da + shfl_xor(da, o);
+        db = db + shfl_xor(db, o);
+      }
+      const R fa = R(-2.0) * da;
+      const R fb = R(-2.0) * dfma(fa, cv[j], db);
+      if (act)
+        for (int i = j + hl; i < k; i += 16) y[i] = dfma(fb, vb[i], dfma(fa, va[i], y[i]));
+      __syncwarp();
+    }
+    if (j == 0) {
+      const R* v = V;
       R dt = 0.0;
       if (act)
-        for (int i = j + 1 + hl; i < k; i += 16) dt = dfma(v[i], y[i], dt);
+        for (int i = 1 + hl; i < k; i += 16) dt = dfma(v[i], y[i], dt);
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) dt = dt + shfl_xor(dt, o);
       const R f = R(-2.0) * dt;
       if (act)
-        for (int i = j + 1 + hl; i < k; i += 16) y[i] = dfma(f, v[i], y[i]);
+        for (int i = 1 + hl; i < k; i += 16) y[i] = dfma(f, v[i], y[i]);
       __syncwarp();
     }
     if (act)
@@ -659,7 +691,7 @@ __device__ TriWork<R> make_triwork(unsigned char* base, const SyevLayout& L) {
 template <typename K>
 static int smem_launch_bytes(K kern, size_t bytes) {
   if (bytes > kSmallSmemBytes) return 0;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+  if (::eig::ensure_dyn_smem(kern, bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -681,7 +713,7 @@ __device__ void syev_in_work(unsigned char* base, const SyevLayout& L, int k, in
   }
   tridiagonalize(a, k, W.d, W.e, V, p, vp);
   tri_eig_lowest(k, m, W, w, red);
-  back_transform(k, m, V, W.Y, W.ldy, Z);
+  back_transform(k, m, V, W.Y, W.ldy, Z, p);
 }
 
 template <typename R, bool SM>
@@ -822,35 +854,52 @@ __device__ void trsm_lower(const R* L, int k, const R* rd, R* X, int ldx, int nc
   }
 }
 
-// X <- L^{-T} X (backward, right-looking), same conventions.
+// X <- L^{-T} X for the same L, X (k x nc), right-looking backward, two rows per barrier
+// (for few columns: every thread finishes the second row for its own columns in registers):
+// on entry to a step rows >= i are final and row i - 1 lacks only row i's update; the step
+// subtracts rows i and i - 1 from the rows above and finishes row i - 2.  Row i - 1 itself is
+// written after the barrier (others read its old value during the step), staged through the
+// double-buffered row nxt (2 * nc scalars).
 template <typename R>
-__device__ void trsm_lower_t(const R* L, int k, const R* rd, R* X, int ldx, int nc) {
+__device__ void trsm_lower_t(const R* L, int k, const R* rd, R* X, int ldx, int nc, R* nxt) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int tc = tid & 15, ti = tid >> 4, nr = nt >> 4;
   for (int c = tid; c < nc; c += nt) X[(k - 1) * ldx + c] *= rd[k - 1];
   __syncthreads();
-  for (int i = k - 1; i > 0; --i) {
-    for (int r = ti; r < i; r += nr) {
-      const R lir = -L[i * k + r];
-      const R s = (r == i - 1) ? rd[r] : R(1.0);
-      for (int c = tc; c < nc; c += 16) {
-        const R v = dfma(lir, X[i * ldx + c], X[r * ldx + c]);
-        X[r * ldx + c] = (r == i - 1) ? v * s : v;
+  int pend = -1;
+  int step = 0;
+  for (int i = k - 1; i > 0; i -= 2, ++step) {
+    R* stage = nxt + (step & 1) * nc;
+    if (pend >= 0 && ti == 0)
+      for (int c = tc; c < nc; c += 16) X[pend * ldx + c] = nxt[((step - 1) & 1) * nc + c];
+    const R l10 = -L[i * k + i - 1], r1 = rd[i - 1];
+    for (int c = tc; c < nc; c += 16) {
+      const R x0 = X[i * ldx + c];
+      const R x1 = dfma(l10, x0, X[(i - 1) * ldx + c]) * r1;
+      if (ti == 0) stage[c] = x1;
+      for (int r = ti; r < i - 1; r += nr) {
+        const R v = dfma(-L[(i - 1) * k + r], x1, dfma(-L[i * k + r], x0, X[r * ldx + c]));
+        X[r * ldx + c] = (r == i - 2) ? v * rd[r] : v;
       }
     }
+    pend = i - 1;
     __syncthreads();
   }
+  if (pend >= 0 && ti == 0)
+    for (int c = tc; c < nc; c += 16) X[pend * ldx + c] = nxt[((step - 1) & 1) * nc + c];
+  __syncthreads();
 }
 
 // Rayleigh-Ritz on (A, G), see small.cuh.
 struct RRLayout {
-  size_t g, dsc, t, syev, z, total;
+  size_t g, dsc, t, syev, z, nx, total;
   SyevLayout S;
   RRLayout(int k, int nb) : S(k, nb) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 127) & ~size_t(127); return r; };
     g = take((size_t)k * k * 8); dsc = take((size_t)k * 2 * 8); t = take((size_t)k * k * 8);
     z = take((size_t)k * nb * 8);
+    nx = take((size_t)2 * k * 8);
     syev = take(S.total);
     total = o;
   }
@@ -872,6 +921,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rr(const double* A, 
   R* dsc = (R*)(work + L.dsc);
   R* t = (R*)(work + L.t);
   R* z = (R*)(work + L.z);
+  R* nx = (R*)(work + L.nx);
   unsigned char* sw = work + L.syev;
   R* a = (R*)(sw + L.S.a);
   // column scaling to a unit-diagonal Gram
@@ -961,7 +1011,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rr(const double* A, 
   __syncthreads();
   syev_in_work(sw, L.S, kk, nb, theta, z, red);
   // C = D L^{-T} Z (in place in z)
-  trsm_lower_t(g, kk, rd, z, nb, nb);
+  trsm_lower_t(g, kk, rd, z, nb, nb, nx);
   if (pivoted) {
     // rows of the taken columns back to their basis positions, zero rows for the others
     for (int idx = tid; idx < k * nb; idx += nt) C[idx] = 0.0;

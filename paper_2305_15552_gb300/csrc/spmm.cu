@@ -451,7 +451,7 @@ size_t spmm_scratch_bytes(const SpmmPlan* P, int nb, eig_dtype vt) {
 template <typename T, typename V, int NB, int WARPS>
 static eig_status launch_rowblock(SpmmPlan* P, const T* X, T* Y, T* Z, size_t sm, cudaStream_t st) {
   auto kern = k_spmm_rowblock<T, V, NB, WARPS>;
-  EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  EIG_CUDA_TRY(::eig::ensure_dyn_smem(kern, (int)sm));
   kern<<<(unsigned)P->nRB, WARPS * 32, sm, st>>>(P->n, P->R, P->C, P->rowptr, P->col,
                                                  static_cast<const V*>(P->val), P->tile_ptr.as<int64_t>(),
                                                  P->tile_col.as<int32_t>(), P->tile_slot.as<int32_t>(), X, Y, Z);

@@ -933,7 +933,7 @@ static eig_status rs_launch(SpmmPlan* P, const T* X, T* Y, int ld, int col0, con
   // X tiles by bulk copy: plain staging of whole, 16-byte aligned rows of a 16-byte multiple
   const int xj_bulk = !Sh::DF && ld == NBK && (Sh::RBY % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
   auto kern = k_spmm_mirror<T, V, NBK, CHEB>;
-  EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  EIG_CUDA_TRY(::eig::ensure_dyn_smem(kern, (int)sm));
   kern<<<(unsigned)P->nRB, kW * 32, sm, st>>>(a, X, Y, ld, col0, xj_bulk, epi);
   EIG_LAUNCH_CHECK(CHEB ? "k_spmm_mirror_cheb" : "k_spmm_mirror");
   return EIG_OK;

@@ -415,7 +415,7 @@ static eig_status tiled_launch_w(SpmmPlan* P, const T* X, T* Y, T* Z, size_t sm,
   a.trp = P->trp.as<uint16_t>();
   a.err = P->err.as<int>();
   auto kern = k_spmm_tiled<T, V, NB, WARPS>;
-  EIG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  EIG_CUDA_TRY(::eig::ensure_dyn_smem(kern, (int)sm));
   kern<<<(unsigned)P->nRB, WARPS * 32, sm, st>>>(a, X, Y, Z);
   EIG_LAUNCH_CHECK("k_spmm_tiled");
   return EIG_OK;
