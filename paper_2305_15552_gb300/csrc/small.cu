@@ -372,8 +372,8 @@ __device__ void tri_eig_lowest(int k, int m, TriWork<R> W, double* w, R* red) {
   glo -= R(1e-12);
   ghi += R(1e-12);
   // multisection.  Round 0: every thread samples one point of [glo, ghi] (shared by all
-  // wanted eigenvalues); eigenvalue t lies where the counts pass t.  Then G threads per
-  // wanted eigenvalue split its bracket into G + 1 parts per round, to the working precision.
+  // wanted eigenvalues); eigenvalue t lies where the counts pass t.  Then G lanes per wanted
+  // eigenvalue split its bracket into G + 1 parts per round, to the working precision.
   // Invariant: count(lo) <= t < count(hi).
   {
     const R x = dfma(ghi - glo, R((float)(tid + 1) / (float)(nt + 1)), glo);
@@ -391,30 +391,35 @@ __device__ void tri_eig_lowest(int k, int m, TriWork<R> W, double* w, R* red) {
     W.hi[t] = (q0 == nt) ? ghi : W.xs[q0];
   }
   __syncthreads();
-  const int G = max(1, nt / m);
+  // rounds 1, 2, ...: G lanes per wanted eigenvalue (G a power of two <= 32, so a warp holds
+  // 32 / G of them), the bracket in registers; a ballot over the lanes' counts picks the
+  // first point above the eigenvalue, with no barrier
+  int G = 32;
+  while (G > 1 && G * m > nt) G >>= 1;
+  const int lane = tid & 31, seg = lane / G, g = lane % G;
+  const int t = (tid >> 5) * (32 / G) + seg;   // this lane's eigenvalue
+  const bool has = t < m;
+  const unsigned segmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (seg * G));
   const float bits = log2f(lead_f32(ghi - glo) / (float)(nt + 1)) - log2f((float)SmallTraits<R>::eps);
   const int rounds = max(0, (int)ceilf(bits / log2f((float)G + 1.0f)));
-  const float frac = (float)((tid % G) + 1) / (float)(G + 1);   // this thread's point in the bracket
+  const float frac = (float)(g + 1) / (float)(G + 1);   // this lane's point in the bracket
+  R lo = has ? W.lo[t] : R(0.0), hi = has ? W.hi[t] : R(1.0);
   for (int r = 0; r < rounds; ++r) {
-    const int t = tid / G;
-    if (t < m) {
-      const R lo = W.lo[t], hi = W.hi[t];
-      const R x = dfma(hi - lo, R(frac), lo);
-      W.xs[tid] = x;
-      W.cnt[tid] = sturm_count(W.ds, W.e2s, k, x);
-    }
-    __syncthreads();
-    if (tid < m) {
-      R nlo = W.lo[tid], nhi = W.hi[tid];
-      for (int gg = 0; gg < G; ++gg) {
-        if (W.cnt[tid * G + gg] <= tid) nlo = W.xs[tid * G + gg];
-        else { nhi = W.xs[tid * G + gg]; break; }
-      }
-      W.lo[tid] = nlo;
-      W.hi[tid] = nhi;
-    }
-    __syncthreads();
+    const R x = dfma(hi - lo, R(frac), lo);
+    const bool below = has && sturm_count(W.ds, W.e2s, k, x) <= t;
+    const unsigned above = ~__ballot_sync(0xffffffffu, below) & segmask;
+    const int q = above ? (__ffs(above) - 1 - seg * G) : G;   // points at or below, in order
+    const R xl = shfl(x, seg * G + max(q - 1, 0));
+    const R xh = shfl(x, seg * G + min(q, G - 1));
+    if (q > 0) lo = xl;
+    if (q < G) hi = xh;
   }
+  __syncthreads();
+  if (has && g == 0) {
+    W.lo[t] = lo;
+    W.hi[t] = hi;
+  }
+  __syncthreads();
   // inverse iteration, one thread per eigenvector, distinct pseudo-random starts, three solves
   // with the factors of T - lam I at the bisected eigenvalue (each contracts the other
   // eigenvectors' components by ~eps ||T|| / gap, which is not small for the tiny eigenvalues
