@@ -168,12 +168,14 @@ EIG_API eig_status eig_spmm_cheb(void* plan, const void* X, void* Y, int nb, eig
 EIG_API eig_status eig_gram(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type, double* G,
                             void* stream);
 
-/* G = A^T B exactly as eig_gram, but without allocating device memory.  For callers that cannot
+/* G = A^T B as eig_gram, but without allocating device memory.  For callers that cannot
  * allocate while they run -- a framework that has reserved the whole device memory for its own
  * pool, or a latency-critical path that must not enter the driver's allocator.  The per-CTA
  * partial sums live in a file-scope __device__ array of 4 MiB (512 partials of a 32 x 32 Gram)
- * that every device loading this library holds until the process exits.  nb <= 32; larger
- * blocks, or more partials than the array holds, return EIG_EINVAL.  The first call on each
+ * that every device loading this library holds until the process exits.  The result is
+ * bitwise equal to eig_gram's while eig_gram's grid (2 CTAs per SM) fits the 512 partials --
+ * always on GB300 (304); on a larger GPU the rows are grouped into 512 partials and the sums
+ * round in another order.  nb <= 32, else EIG_EINVAL.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
  * make that first call before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be serialised by the
@@ -181,6 +183,11 @@ EIG_API eig_status eig_gram(const void* A, const void* B, int64_t n, int nb, eig
  * The paper has no counterpart to this entry point. */
 EIG_API eig_status eig_gram_noalloc(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type,
                                     double* G, void* stream);
+
+/* eig_gram_noalloc with the CTA partials capped at max_parts (1..512, else EIG_EINVAL): the
+ * grouping a GPU with more than 256 SMs would get, for checking that path on this one. */
+EIG_API eig_status eig_gram_noalloc_parts(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type,
+                                          double* G, int max_parts, void* stream);
 
 /* CholeskyQR2 (Alg. 3 "CholeskyQR"; applied twice): X (device, n x k, vec_type, in place) becomes
  * Q with X_in = Q R, R (device FP64 k x k, upper triangular) = R2 R1.  k <= 64.  Returns
@@ -378,11 +385,14 @@ typedef struct {
 EIG_API eig_status eig_autotune_spmm(const eig_csr_upper* H, int nb, eig_dtype vec_type, int reps,
                                      eig_tune_result* best, eig_tune_result* all, int* n_all, void* stream);
 
-/* The Chebyshev degree d of Alg. 3 for this handle's matrix: runs the ChebFSI solve (opts from
- * base, NULL = defaults; cheb_degree and timing overridden) once per degrees[i] and returns in
- * *best_degree the degree of the fastest solve that converged (time_ms_total); ms[i] and
- * converged[i] (may be NULL) receive each run's time and status.  The handle keeps the result
- * of the last run.  EIG_ENOT_CONVERGED (and *best_degree = 0) when no degree converged.
+/* The Chebyshev degree d of Alg. 3 for this handle's matrix: after one untimed warm-up solve,
+ * runs the ChebFSI solve (opts from base, NULL = defaults; cheb_degree and timing overridden)
+ * three times per degrees[i] and returns in *best_degree the degree with the smallest median
+ * time_ms_total among those whose runs all converged; ms[i] (the median, 0 when not a
+ * candidate) and converged[i] (may be NULL) receive each degree's result.  A degree whose
+ * solve does not converge, returns duplicate pairs or breaks down is skipped, not fatal.  The
+ * handle keeps the result of the last run.  EIG_ENOT_CONVERGED (and *best_degree = 0) when no
+ * degree converged; CUDA, allocation and argument errors are returned at once.
  * Synchronises base->stream. */
 EIG_API eig_status eig_autotune_cheb(void* handle, const int* degrees, int count, const eig_opts* base,
                                      int* best_degree, double* ms, int* converged);

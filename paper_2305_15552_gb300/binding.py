@@ -89,6 +89,8 @@ _SIGS = {
                                 C.c_double, C.c_double, C.c_int, C.c_void_p]),
     "eig_gram": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "eig_gram_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "eig_gram_noalloc_parts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                         C.c_void_p]),
     "eig_cholqr2": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "eig_small_syev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "eig_small_rr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
@@ -280,14 +282,19 @@ def gram(A, B):
     return G
 
 
-def gram_noalloc(A, B):
-    """G = A^T B through eig_gram_noalloc (no device allocation; scratch in a fixed device array)."""
+def gram_noalloc(A, B, max_parts=None):
+    """G = A^T B through eig_gram_noalloc (no device allocation; scratch in a fixed device array);
+    max_parts caps the CTA partials (eig_gram_noalloc_parts)."""
     import torch
     lib = load()
     assert A.shape == B.shape and A.dtype == B.dtype and A.is_contiguous() and B.is_contiguous()
     G = torch.empty(A.shape[1], A.shape[1], dtype=torch.float64, device=A.device)
-    check(lib.eig_gram_noalloc(_ptr(A), _ptr(B), A.shape[0], A.shape[1], vec_dtype(A), _ptr(G), stream_ptr()),
-          "eig_gram_noalloc")
+    if max_parts is None:
+        check(lib.eig_gram_noalloc(_ptr(A), _ptr(B), A.shape[0], A.shape[1], vec_dtype(A), _ptr(G), stream_ptr()),
+              "eig_gram_noalloc")
+    else:
+        check(lib.eig_gram_noalloc_parts(_ptr(A), _ptr(B), A.shape[0], A.shape[1], vec_dtype(A), _ptr(G),
+                                         int(max_parts), stream_ptr()), "eig_gram_noalloc_parts")
     return G
 
 

@@ -16,7 +16,8 @@ namespace {
 
 // 4 MiB of partials: up to 512 CTA partials of a 32 x 32 Gram.
 constexpr int kNoAllocParts = 512;
-constexpr size_t kNoAllocScratchDoubles = (size_t)kNoAllocParts * 32 * 32;
+constexpr int kNoAllocMaxBlock = 32;
+constexpr size_t kNoAllocScratchDoubles = (size_t)kNoAllocParts * kNoAllocMaxBlock * kNoAllocMaxBlock;
 __device__ __align__(256) double g_gram_scratch[kNoAllocScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -45,11 +46,13 @@ using namespace eig;
 
 extern "C" {
 
-eig_status eig_gram_noalloc(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type, double* G,
-                            void* stream) {
-  if (!A || !B || !G || n < 1 || nb < 1 || nb > 32) return EIG_EINVAL;
+eig_status eig_gram_noalloc_parts(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type, double* G,
+                                  int max_parts, void* stream) {
+  static_assert((size_t)kNoAllocParts * kNoAllocMaxBlock * kNoAllocMaxBlock <= kNoAllocScratchDoubles,
+                "the scratch array holds every partial of the largest block");
+  if (!A || !B || !G || n < 1 || nb < 1 || nb > kNoAllocMaxBlock) return EIG_EINVAL;
   if (vec_type != EIG_F32 && vec_type != EIG_F64) return EIG_EINVAL;
-  if ((size_t)kNoAllocParts * nb * nb > kNoAllocScratchDoubles) return EIG_EINVAL;
+  if (max_parts < 1 || max_parts > kNoAllocParts) return EIG_EINVAL;
   void* scratch = nullptr;
   EIG_TRY(scratch_address(&scratch));
   BlockList bl;
@@ -58,7 +61,12 @@ eig_status eig_gram_noalloc(const void* A, const void* B, int64_t n, int nb, eig
   bl.p[1] = B;
   const int pa = 0, pb = 1;
   // every CTA overwrites all of its partials, so the array needs no clearing between calls
-  return gram_multi(bl, &pa, &pb, 1, nb, n, vec_type, G, scratch, as_stream(stream), kNoAllocParts);
+  return gram_multi(bl, &pa, &pb, 1, nb, n, vec_type, G, scratch, as_stream(stream), max_parts);
+}
+
+eig_status eig_gram_noalloc(const void* A, const void* B, int64_t n, int nb, eig_dtype vec_type, double* G,
+                            void* stream) {
+  return eig_gram_noalloc_parts(A, B, n, nb, vec_type, G, kNoAllocParts, stream);
 }
 
 }  // extern "C"
