@@ -24,6 +24,7 @@ N > 1 runs under torchrun: every rank solves its own replica (replicas only: the
 data-parallel exchange on one node here), timing is max over ranks.
 """
 import argparse
+import dataclasses
 import json
 import os
 import platform
@@ -199,17 +200,38 @@ def make_problem(args):
     return H, time.time() - t
 
 
+def pinned(a, keep):
+    """A copy of numpy array a in page-locked host memory (a numpy view of a pinned torch
+    buffer, which `keep` holds alive)."""
+    import torch
+    a = np.ascontiguousarray(a)
+    buf = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True)
+    keep.append(buf)
+    v = buf.numpy().view(a.dtype).reshape(a.shape)
+    v[...] = a
+    return v
+
+
 def initial_guess(H, args, binding):
     """Zero-padded lowest n_b eigenvectors of the leading n/10 principal block (the smaller model
-    space of Sec. 3.1), solved on the GPU by LOBPCG with FP64 vectors to relative residual 1e-8."""
+    space of Sec. 3.1), solved on the GPU by LOBPCG with FP64 vectors to relative residual 1e-8,
+    itself started from the padded eigenvectors of its own leading block of at most 20,000 rows
+    (LOBPCG from a seeded random block).  A random block straight on n/10 rows can leave the
+    shifted Jacobi preconditioner on an interior cluster of these spectra, whose lowest pairs are
+    localised in the first rows."""
     from gen import principal_submatrix, pad_rows
     n0 = max(args.nb * 8, H.n // 10)
-    H0 = principal_submatrix(H, n0)
-    S0 = binding.Solver(H0, args.nb, args.nb)
-    rc, st = S0.solve("lobpcg", vec_type="f64", tol=1e-8, maxiter=1000, seed=args.seed)
-    _, X0, _ = S0.ritz()
-    S0.close()
-    return pad_rows(X0, H.n)
+    n00 = max(args.nb * 8, min(20000, n0 // 10))
+    X = None
+    for m in (n00, n0):
+        S0 = binding.Solver(principal_submatrix(H, m), args.nb, args.nb)
+        if X is None:
+            S0.solve("lobpcg", vec_type="f64", tol=1e-8, maxiter=1000, seed=args.seed)
+        else:
+            S0.solve("lobpcg", X0=pad_rows(X, m), vec_type="f64", tol=1e-8, maxiter=1000)
+        X = S0.ritz()[1]
+        S0.close()
+    return pad_rows(X, H.n)
 
 
 def oracle_sample(H, args, threads):
@@ -308,7 +330,8 @@ def workload_config(args, H):
             "n": H.n, "nnz_half": H.nnz, "n_ev": args.nev, "block": args.nb, "values": args.storage,
             "vectors": args.vec, "layout": args.layout, "switch_res": args.switch_res,
             "switch_tau": args.switch_tau, "switch_gap": getattr(args, "switch_gap", 0.0), "s_max": args.s_max,
-            "l2": "inputs larger than L2 (matrix ~3.2 GB), no flush",
+            "l2": (f"inputs larger than L2 (stored matrix ~{(H.rowptr.nbytes + H.col.nbytes + H.val.nbytes) / 1e9:.1f} GB), "
+                   "no flush"),
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
@@ -551,7 +574,11 @@ SHAPE_NAMES = {0: "FP32 vectors, nb 1", 1: "FP32 vectors, nb 2", 2: "FP32 vector
 # one capture of the 500,000-row matrix of the same generator, ~400 nnz/row), per entry of the layout
 # (the layout streams every entry once per product, so traffic grows in proportion to the entries);
 # valid only for the kernel source whose SHA-256 prefix is `kernel_sha` (None after the kernel changed).
-SPMM_TRAFFIC = {"kernel_sha": None, "per_layout_entry": {}}
+# DRAM bytes per layout entry of k_spmm_mirror, from one ncu capture per shape at n = 500,000
+# (dram__bytes_read.sum + dram__bytes_write.sum over the plan's layout entries, 2.04e8); keyed
+# by the shape index 6 * (FP64 vectors) + log2(nb); void once spmm_mirror.cu changes.
+SPMM_TRAFFIC = {"kernel_sha": "972837db70c61e29", "per_layout_entry": {4: 1.311066e9 / 204360448, 3: 1.266528e9 / 204360448,
+                                                          9: 1.336002e9 / 204360448}}
 
 
 def kernel_sha():
@@ -657,20 +684,26 @@ def run_hybrid(args, ws, rank, local):
     S.close()
     threads = os.cpu_count() or 1
     true_rel, dl_bound = certify(H, th, X, threads)
-    # end to end through the C ABI from host buffers
+    # end to end through the C ABI from pinned host buffers: H and X0 copied in (and H planned),
+    # the eigenvectors copied back, every step
     e2e_ms = []
     h2d = H.rowptr.nbytes + H.col.nbytes + H.val.nbytes + X0.nbytes
     d2h = H.n * args.nev * 8 + 2 * args.nev * 8
+    keep = []
+    Hp = dataclasses.replace(H, rowptr=pinned(H.rowptr, keep), col=pinned(H.col, keep), val=pinned(H.val, keep))
+    X0p = pinned(X0, keep)
+    Xout = pinned(np.zeros((H.n, args.nev)), keep)
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        S2 = binding.Solver(H, args.nev, args.nb, layout=args.layout)
-        S2.solve("hybrid", X0=X0, vec_type=args.vec, tol=args.tol, maxiter=500, rmm_precond=args.rmm_precond,
+        S2 = binding.Solver(Hp, args.nev, args.nb, layout=args.layout)
+        S2.solve("hybrid", X0=X0p, vec_type=args.vec, tol=args.tol, maxiter=500, rmm_precond=args.rmm_precond,
                  switch_res=args.switch_res, switch_tau=args.switch_tau, switch_gap=args.switch_gap, s_max=args.s_max)
-        S2.ritz()
+        S2.ritz(out=Xout)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t) * 1e3)
         S2.close()
+    del Hp, X0p, Xout, keep
     e2e = reduce_max(min(e2e_ms), ws, "cuda") if e2e_ms else None
     peak, peak_kind = measured_peak()
     achieved = (acc["spmm_bytes"] / max(acc["time_ms_spmm"], 1e-9)) / 1e6  # GB/s over every timed SpMM
@@ -895,10 +928,11 @@ def run_sweep(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus, "steps": 1, "warmup": 1,
         "ms_per_step": value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": "f64", "data": "synthetic",
         "config": {"workload": (f"switch-point sweep (Sec. 4): paper-shaped n={H.n:,}, ~{args.sweep_nnz_per_row:g} "
                                 f"nnz/row, block pattern {args.block_pattern}, half-stored nnz={H.nnz:,}, FP32 "
-                                f"values/vectors, tol {args.tol:g}, RMM-DIIS as printed (no safety net); value = "
+                                f"values, FP64 vectors (the paper's arithmetic for the vectors), Jacobi K in the front, "
+                                f"unpreconditioned RMM-DIIS, tol {args.tol:g}, RMM-DIIS as printed (no safety net); value = "
                                 f"LOBPCG -> RMM-DIIS at tau <= 1e-7, n_ev=5, n_b=8"),
                    "n": H.n, "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "matrix ~0.9 GB, larger than L2; no flush"},

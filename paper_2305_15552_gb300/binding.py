@@ -433,8 +433,9 @@ class Solver:
             st["trace"] = tr[: stats.trace_rows].copy()
         return rc, st
 
-    def ritz(self, X_on_device=False):
-        """(theta[n_ev], X (n x n_ev FP64; numpy or torch), relres[n_ev])."""
+    def ritz(self, X_on_device=False, out=None):
+        """(theta[n_ev], X (n x n_ev FP64; numpy or torch), relres[n_ev]).  out: a C-contiguous
+        FP64 host array (n x n_ev) to receive X (e.g. in page-locked memory)."""
         import numpy as np
         th = np.zeros(self.n_ev)
         rel = np.zeros(self.n_ev)
@@ -443,7 +444,11 @@ class Solver:
             X = torch.empty(self.n, self.n_ev, dtype=torch.float64, device="cuda")
             check(self._lib.eig_ritz(self._h, _ptr(th), _ptr(X), _ptr(rel), 1), "eig_ritz")
         else:
-            X = np.zeros((self.n, self.n_ev))
+            if out is not None:
+                assert out.dtype == np.float64 and out.shape == (self.n, self.n_ev) and out.flags.c_contiguous
+                X = out
+            else:
+                X = np.zeros((self.n, self.n_ev))
             check(self._lib.eig_ritz(self._h, _ptr(th), _ptr(X), _ptr(rel), 0), "eig_ritz")
         return th, X, rel
 
