@@ -314,6 +314,9 @@ SPMM_KERNELS = {1: "k_spmm_mirror (mirrored tiles, gather only)",
                 3: "k_spmm_rowblock + k_spmm_transpose_reduce (CSR)"}
 
 
+VAL_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
+
+
 def workload_config(args, H):
     rmm = "Jacobi-preconditioned RMM-DIIS" if args.rmm_precond else "RMM-DIIS"
     sw = []
@@ -330,8 +333,8 @@ def workload_config(args, H):
             "n": H.n, "nnz_half": H.nnz, "n_ev": args.nev, "block": args.nb, "values": args.storage,
             "vectors": args.vec, "layout": args.layout, "switch_res": args.switch_res,
             "switch_tau": args.switch_tau, "switch_gap": getattr(args, "switch_gap", 0.0), "s_max": args.s_max,
-            "l2": (f"inputs larger than L2 (stored matrix ~{(H.rowptr.nbytes + H.col.nbytes + H.val.nbytes) / 1e9:.1f} GB), "
-                   "no flush"),
+            "l2": (f"inputs larger than L2 (stored matrix ~{(8 * (H.n + 1) + H.nnz * (4 + VAL_BYTES[args.storage])) / 1e9:.1f}"
+                   " GB), no flush"),
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
