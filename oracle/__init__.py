@@ -25,7 +25,7 @@ from .dense import lowest_eigpairs, eigh_sorted
 from .blocks import gram, cholqr, cholqr2, rayleigh_ritz, rayleigh_ritz_projected, orthonormal_basis
 from .precond import jacobi_apply
 from .lanczos import lanczos
-from .block_lanczos import block_lanczos
+from .block_lanczos import block_lanczos, thick_restart
 from .lobpcg import lobpcg
 from .chebfsi import chebfsi, lambda_ub_estimate, cheb_filter
 from .rmmdiis import rmmdiis, diis_coefficients, diis_extrapolate, rr2
