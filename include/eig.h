@@ -278,6 +278,17 @@ typedef struct {
                            /* eigenvector, where RMM-DIIS (which converges to the eigenvector        */
                            /* nearest its start, Sec. 3.3) converges to the right one; 0 = off       */
                            /* (default).  Ignored with switch_after.                                 */
+  int lanczos_keep;        /* block Lanczos thick restart (Sec. 2.2, restart after d iterations):   */
+                           /* when the basis holds lanczos_maxbasis vectors (at most 62 blocks),    */
+                           /* restart from the lowest lanczos_keep Ritz vectors (rounded up to a    */
+                           /* multiple of the block, at least n_ev, at most 256 and one block below */
+                           /* the basis) and the residual block; 0 (default) = half the basis;      */
+                           /* -1 = no restart: stop at the basis limit                              */
+  int rmm_decouple;        /* decoupled RMM-DIIS (Sec. 4.3): once this many wanted eigenvectors     */
+                           /* have converged, each iteration forms H r~ by one SpMV per remaining   */
+                           /* vector instead of one SpMM over the block (the same sums, so the same */
+                           /* iterates); 0 (default) = coupled (SpMM) throughout.  Mirrored SpMM    */
+                           /* layout only; other layouts stay coupled.                              */
 } eig_opts;
 
 typedef struct {

@@ -50,7 +50,8 @@ class Opts(C.Structure):
                 ("X0", C.c_void_p), ("x0_cols", C.c_int), ("x0_on_device", C.c_int), ("seed", C.c_uint64),
                 ("certify", C.c_int), ("timing", C.c_int), ("stream", C.c_void_p), ("trace", C.c_void_p),
                 ("trace_cap", C.c_int), ("rmm_maxiter", C.c_int), ("rmm_fallback", C.c_int),
-                ("diis_tol", C.c_double), ("lp_params", C.c_void_p), ("switch_gap", C.c_double)]
+                ("diis_tol", C.c_double), ("lp_params", C.c_void_p), ("switch_gap", C.c_double),
+                ("lanczos_keep", C.c_int), ("rmm_decouple", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -184,6 +184,23 @@ __global__ void k_put_blocks(double* __restrict__ T, int ld, int i, int nb, cons
   }
 }
 
+// After a thick restart: the couplings of the kept Ritz vectors (blocks 0..q-1) to block q,
+// C_b = V_b^T H V_q, into T's column block q and row block q.
+__global__ void k_put_coupling(double* __restrict__ T, int ld, int q, int nb, const double* __restrict__ C) {
+  const int tot = q * nb * nb;
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < tot; e += blockDim.x * gridDim.x) {
+    const int b = e / (nb * nb), a = (e / nb) % nb, col = e % nb;
+    const double v = C[e];
+    T[(size_t)(b * nb + a) * ld + q * nb + col] = v;
+    T[(size_t)(q * nb + col) * ld + b * nb + a] = v;
+  }
+}
+
+// T (ld x ld, zeroed by the caller) <- diag(theta_0 .. theta_{p-1}) in its leading p x p
+__global__ void k_set_diag(double* __restrict__ T, int ld, const double* __restrict__ theta, int p) {
+  for (int i = threadIdx.x; i < p; i += blockDim.x) T[(size_t)i * ld + i] = theta[i];
+}
+
 // copy the leading k x k of a matrix with leading dimension ld into a dense k x k
 __global__ void k_copy_lead(const double* __restrict__ T, int ld, int k, double* __restrict__ out) {
   for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < k * k; e += blockDim.x * gridDim.x)
@@ -420,16 +437,29 @@ eig_status run_block_lanczos(Ctx& c, const double* X0, int x0c, int maxiter, con
   const eig_dtype vt = c.o.vec_type;
   const size_t sv = dtype_size(vt);
   const int maxblocks = std::max(2, std::min({c.o.lanczos_maxbasis / nb, 62, (int)(n / nb)}));
+  // thick restart (Sec. 2.2): when the basis holds maxblocks blocks, keep the lowest `keep` Ritz
+  // vectors (a multiple of nb, at least n_ev, leaving room for one more block) and continue
+  const int nevb = ((nev + nb - 1) / nb) * nb;
+  int keep = 0;
+  if (c.o.lanczos_keep >= 0) {
+    int kk = c.o.lanczos_keep > 0 ? ((c.o.lanczos_keep + nb - 1) / nb) * nb : (maxblocks / 2) * nb;
+    kk = std::min(std::max(kk, nevb), 256 / nb * nb);
+    if (kk >= nevb && kk <= (maxblocks - 1) * nb) keep = kk;
+  }
+  const int qkeep = keep / nb;
+  const int mz = std::max(nev, keep);   // columns of Z: the wanted pairs, or the kept ones at a restart
   const size_t blk = (size_t)n * nb * sv;
-  EIG_TRY(h->big.reserve((size_t)(maxblocks + 3) * blk + 512));
+  EIG_TRY(h->big.reserve((size_t)(maxblocks + 3 + qkeep) * blk + 512));
   std::vector<void*> V(maxblocks + 1);
   for (int b = 0; b <= maxblocks; ++b) V[b] = (unsigned char*)h->big.p + (size_t)b * blk;
   void* HV = (unsigned char*)h->big.p + (size_t)(maxblocks + 1) * blk;
   void* W = (unsigned char*)h->big.p + (size_t)(maxblocks + 2) * blk;
+  unsigned char* Ytmp = (unsigned char*)h->big.p + (size_t)(maxblocks + 3) * blk;   // qkeep blocks
   const int kmax = maxblocks * nb;
   const size_t gsz = gram_scratch_bytes(15, nb);
-  const size_t sm = (size_t)kmax * kmax * 8 * 2 + (size_t)(maxblocks + 1) * nb * nb * 8 * 2 + (size_t)kmax * nev * 8 +
-                    small_syev_work_bytes(kmax, nev) + gsz + 64 * 256 + (size_t)nb * nb * 8 * 2;
+  const size_t sm = (size_t)kmax * kmax * 8 * 2 + (size_t)(maxblocks + 1) * nb * nb * 8 * 2 + (size_t)kmax * mz * 8 +
+                    small_syev_work_bytes(kmax, mz) + gsz + 256 * 8 * 3 + (size_t)nb * nb * 8 * 2 +
+                    (size_t)kmax * nb * 8 + 5 * 256;
   EIG_TRY(h->small.reserve(sm));
   unsigned char* p = (unsigned char*)h->small.p;
   auto take = [&](size_t b) { unsigned char* r = p; p += (b + 255) & ~size_t(255); return r; };
@@ -437,12 +467,13 @@ eig_status run_block_lanczos(Ctx& c, const double* X0, int x0c, int maxiter, con
   double* Tk = (double*)take((size_t)kmax * kmax * 8);
   double* Cc = (double*)take((size_t)(maxblocks + 1) * nb * nb * 8);
   double* M = (double*)take((size_t)(maxblocks + 1) * nb * nb * 8);
-  double* Z = (double*)take((size_t)kmax * nev * 8);
-  double* wv = (double*)take(64 * 8);
-  double* est = (double*)take(64 * 8);
-  double* estp = (double*)take(64 * 8);
+  double* Z = (double*)take((size_t)kmax * mz * 8);
+  double* wv = (double*)take(256 * 8);
+  double* est = (double*)take(256 * 8);
+  double* estp = (double*)take(256 * 8);
   double* R = (double*)take((size_t)nb * nb * 8);
-  void* work = take(small_syev_work_bytes(kmax, nev));
+  double* Zb = (double*)take((size_t)kmax * nb * 8);   // one block of columns of Z at a restart
+  void* work = take(small_syev_work_bytes(kmax, mz));
   void* gpart = take(gsz);
   EIG_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)kmax * kmax * 8, c.st));
   // V_1 = orthonormal basis of X0 (Alg. 1 line 1)
@@ -465,11 +496,17 @@ eig_status run_block_lanczos(Ctx& c, const double* X0, int x0c, int maxiter, con
   std::vector<double> th(nev, 0.0), rel(nev, 0.0);
   *converged = false;
   *reason = 0;
-  int it = 0, nblocks = 1, kdim = nb;
+  int it = -1, nblocks = 1, kdim = nb, restart_at = -1;
   for (int i = 0;; ++i) {
+    ++it;
     // H V_i and CGS2 against the basis (Eq. bgs)
     EIG_TRY(c.spmm(V[i], HV, nb, vt, nb));
     EIG_TRY(basis_gram(c, V.data(), i + 1, HV, nb, vt, Cc, gpart));
+    if (i == restart_at) {
+      // first block after a thick restart: H Y = Y Theta + V_q S, so T's kept rows couple to it
+      k_put_coupling<<<4, 256, 0, c.st>>>(T, kmax, i, nb, Cc);
+      EIG_LAUNCH_CHECK("k_put_coupling");
+    }
     k_put_blocks<<<1, 256, 0, c.st>>>(T, kmax, i, nb, Cc + (size_t)i * nb * nb, nullptr);
     EIG_LAUNCH_CHECK("k_put_blocks");
     {
@@ -518,14 +555,36 @@ eig_status run_block_lanczos(Ctx& c, const double* X0, int x0c, int maxiter, con
       rel[t] = hs[64 + t];
       conv = conv && rel[t] < c.o.tol;
     }
-    it = i;
-    c.trace(0, i, th.data(), rel.data(), m);
+    c.trace(0, it, th.data(), rel.data(), m);
     if (conv) { *converged = true; break; }
     if (!qr_ok) { *reason = 4; break; }
-    if (i + 1 >= maxblocks || it >= maxiter) break;
+    if (it >= maxiter) break;
     if (stop) {
       const int r = stop(it + 1, th.data(), rel.data(), m);
       if (r) { *reason = r; break; }
+    }
+    if (i + 1 >= maxblocks) {
+      if (keep == 0) break;   // no restart: stop at the basis limit
+      // thick restart (Sec. 2.2): Y = V Z(:, 1:keep) replaces the basis, V_{i+1} follows it,
+      // T = diag(theta_1..keep) until the next block's Gram adds the couplings
+      EIG_TRY(small_syev(Tk, kdim, keep, wv, Z, work, nullptr, c.st));
+      BlockList in;
+      in.n = i + 1;
+      for (int b = 0; b <= i; ++b) in.p[b] = V[b];
+      for (int b = 0; b < qkeep; ++b) {
+        EIG_CUDA_TRY(cudaMemcpy2DAsync(Zb, nb * 8, Z + b * nb, (size_t)keep * 8, nb * 8, kdim,
+                                       cudaMemcpyDeviceToDevice, c.st));
+        EIG_TRY(block_apply(in, nb, Zb, nb, Ytmp + (size_t)b * blk, 0.0, n, vt, c.st));
+      }
+      for (int b = 0; b < qkeep; ++b)
+        EIG_CUDA_TRY(cudaMemcpyAsync(V[b], Ytmp + (size_t)b * blk, blk, cudaMemcpyDeviceToDevice, c.st));
+      EIG_CUDA_TRY(cudaMemcpyAsync(V[qkeep], V[i + 1], blk, cudaMemcpyDeviceToDevice, c.st));
+      EIG_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)kmax * kmax * 8, c.st));
+      k_set_diag<<<1, 256, 0, c.st>>>(T, kmax, wv, keep);
+      EIG_LAUNCH_CHECK("k_set_diag");
+      restart_at = qkeep;
+      i = qkeep - 1;
+      continue;
     }
     // append R_{i+1} to T
     k_put_blocks<<<1, 256, 0, c.st>>>(T, kmax, i, nb, nullptr, R);

@@ -197,6 +197,38 @@ eig_status Ctx::spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_
   return EIG_OK;
 }
 
+eig_status Ctx::spmv_col(const void* X, void* Y, int ld, int col, eig_dtype vt) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (o.timing) {
+    EIG_CUDA_TRY(cudaEventCreate(&a));
+    EIG_CUDA_TRY(cudaEventCreate(&b));
+    EIG_CUDA_TRY(cudaEventRecord(a, st));
+  }
+  const eig_status r = spmm_run_column(&h->plan, X, Y, ld, col, vt, st);
+  if (r != EIG_OK) {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return r;
+  }
+  if (o.timing) {
+    EIG_CUDA_TRY(cudaEventRecord(b, st));
+    spmm_ev.emplace_back(a, b);
+  }
+  count_spmm(1, vt, 1);
+  return EIG_OK;
+}
+
+eig_status Ctx::rmm_product(const void* X, void* Y, int mp, eig_dtype vt, const std::vector<int>& act, int nev) {
+  int nact = 0;
+  for (int j = 0; j < mp; ++j) nact += act[j];
+  if (o.rmm_decouple > 0 && nev - nact >= o.rmm_decouple && h->plan.mirrored) {
+    for (int j = 0; j < mp; ++j)
+      if (act[j]) EIG_TRY(spmv_col(X, Y, mp, j, vt));
+    return EIG_OK;
+  }
+  return spmm(X, Y, mp, vt, nact);
+}
+
 eig_status Ctx::spmm_cheb(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols, const void* Qp,
                           const int* active, double alpha, double cshift, int first) {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -794,7 +826,7 @@ static eig_status run_rmmdiis_mixed(Ctx& c, const double* X0, int maxiter, int* 
     } else if (c.o.rmm_precond) {
       EIG_TRY(rmx_precond(xt, rraw, s1, tref, active, h->plan.diag.as<double>(), c.o.precond_floor, mp, n, w, c.st));
     }
-    EIG_TRY(c.spmm(w, hw, mp, EIG_F32, nact));
+    EIG_TRY(c.rmm_product(w, hw, mp, EIG_F32, act, nev));
     EIG_TRY(rmx_dots(xt, w, rraw, hw, tref, mp, n, part, &np, c.st));
     EIG_TRY(reduce_partials(part, np, mp * 5, s2, c.st));
     EIG_TRY(rmx_rr2(s1, s2, tref, active, mp, theta, par, c.st));
@@ -950,7 +982,7 @@ eig_status run_rmmdiis(Ctx& c, const double* X0, int maxiter, int* iters, bool* 
                                 c.st));
     int nact = 0;
     for (int j = 0; j < mp; ++j) nact += act[j];
-    EIG_TRY(c.spmm(rt, hrt, mp, vt, nact));
+    EIG_TRY(c.rmm_product(rt, hrt, mp, vt, act, nev));
     {
       const int threads = (256 / mp) * mp;
       if (vt == EIG_F32) k_rmm_dots4<float><<<grid, threads, 0, c.st>>>(xt, (const float*)rt, (const float*)hrt, mp, n, part);
@@ -1031,6 +1063,8 @@ void eig_default_opts(eig_opts* o) {
   o->cheb_degree = 10;
   o->lambda_ub = 0.0;
   o->lanczos_maxbasis = 600;
+  o->lanczos_keep = 0;
+  o->rmm_decouple = 0;
   o->X0 = nullptr;
   o->x0_cols = 0;
   o->x0_on_device = 0;

@@ -55,6 +55,11 @@ struct Ctx {
   std::vector<int> spmm_shape;   // product shape of each timed call (index of eig_stats' by-shape arrays)
   void count_spmm(int nb, eig_dtype vt, int64_t spmv_cols);
   eig_status spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols);
+  // one SpMV: column col of a block with row stride ld (decoupled RMM-DIIS, Sec. 4.3)
+  eig_status spmv_col(const void* X, void* Y, int ld, int col, eig_dtype vt);
+  // H r for the RMM-DIIS block: one SpMM, or (decoupled, once opts.rmm_decouple wanted vectors
+  // have converged) one SpMV per active column
+  eig_status rmm_product(const void* X, void* Y, int mp, eig_dtype vt, const std::vector<int>& act, int nev);
   // spmm with a fused Chebyshev step (spmm_run_cheb); EIG_EUNSUPPORTED leaves Y untouched
   eig_status spmm_cheb(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols, const void* Qp,
                        const int* active, double alpha, double cshift, int first);

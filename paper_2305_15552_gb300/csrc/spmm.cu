@@ -510,6 +510,9 @@ static eig_status launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st) {
 }
 
 template <typename T, typename V>
+eig_status mirror_launch_column(SpmmPlan* P, const T* X, T* Y, int ld, int col, cudaStream_t st);
+
+template <typename T, typename V>
 static eig_status dispatch_nb(SpmmPlan* P, const T* X, T* Y, T* Z, int nb, cudaStream_t st) {
   switch (nb) {
     case 1: return launch<T, V, 1>(P, X, Y, Z, st);
@@ -544,6 +547,27 @@ eig_status spmm_run_with_scratch(SpmmPlan* P, const void* X, void* Y, int nb, ei
     if (P->val_type == EIG_F64) return dispatch_nb<double, double>(P, x, y, z, nb, st);
     if (P->val_type == EIG_F32) return dispatch_nb<double, float>(P, x, y, z, nb, st);
     if (P->val_type == EIG_BF16) return dispatch_nb<double, uint16_t>(P, x, y, z, nb, st);
+    return EIG_EUNSUPPORTED;
+  }
+  return EIG_EINVAL;
+}
+
+eig_status spmm_run_column(SpmmPlan* P, const void* X, void* Y, int ld, int col, eig_dtype vt, cudaStream_t st) {
+  if (!P || !X || !Y || ld < 1 || col < 0 || col >= ld) return EIG_EINVAL;
+  if (!P->mirrored) return EIG_EUNSUPPORTED;
+  if (vt == EIG_F32) {
+    const float* x = static_cast<const float*>(X);
+    float* y = static_cast<float*>(Y);
+    if (P->val_type == EIG_F32) return mirror_launch_column<float, float>(P, x, y, ld, col, st);
+    if (P->val_type == EIG_BF16) return mirror_launch_column<float, uint16_t>(P, x, y, ld, col, st);
+    return EIG_EUNSUPPORTED;
+  }
+  if (vt == EIG_F64) {
+    const double* x = static_cast<const double*>(X);
+    double* y = static_cast<double*>(Y);
+    if (P->val_type == EIG_F64) return mirror_launch_column<double, double>(P, x, y, ld, col, st);
+    if (P->val_type == EIG_F32) return mirror_launch_column<double, float>(P, x, y, ld, col, st);
+    if (P->val_type == EIG_BF16) return mirror_launch_column<double, uint16_t>(P, x, y, ld, col, st);
     return EIG_EUNSUPPORTED;
   }
   return EIG_EINVAL;

@@ -84,6 +84,9 @@ size_t mirror_bytes_estimate(const SpmmPlan* P);
 // Builds the tile-contiguous copy (called by spmm_plan_build).
 eig_status spmm_plan_build_tiled(SpmmPlan* P, int cap, cudaStream_t st);
 eig_status spmm_run(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, cudaStream_t st);
+// Y(:, col) = H X(:, col) for blocks with row stride ld (one SpMV; mirrored layout only, else
+// EIG_EUNSUPPORTED).
+eig_status spmm_run_column(SpmmPlan* P, const void* X, void* Y, int ld, int col, eig_dtype vt, cudaStream_t st);
 // Scratch bytes spmm_run needs for (nb, vec type); caller-provided scratch variant below.
 size_t spmm_scratch_bytes(const SpmmPlan* P, int nb, eig_dtype vt);
 eig_status spmm_run_with_scratch(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, void* scratch,

@@ -946,6 +946,13 @@ eig_status mirror_launch(SpmmPlan* P, const T* X, T* Y, cudaStream_t st) {
   return EIG_OK;
 }
 
+// One column of X (row stride ld, column col) times H into the same column of Y: the SpMV of
+// a decoupled RMM-DIIS vector (Sec. 4.3), summed in the order of the block product's column.
+template <typename T, typename V>
+eig_status mirror_launch_column(SpmmPlan* P, const T* X, T* Y, int ld, int col, cudaStream_t st) {
+  return rs_launch<T, V, 1, false>(P, X, Y, ld, col, MirrorEpi(), st);
+}
+
 // The Chebyshev-step variant (same kernel, fused epilogue).
 template <typename T, typename V, int NB>
 eig_status mirror_launch_cheb(SpmmPlan* P, const T* X, T* Y, const T* Qp, const int* active, double alpha, double c,
@@ -984,5 +991,12 @@ EIG_MIRROR_INST(float, uint16_t)
 EIG_MIRROR_INST(double, double)
 EIG_MIRROR_INST(double, float)
 EIG_MIRROR_INST(double, uint16_t)
+
+template eig_status mirror_launch_column<float, float>(SpmmPlan*, const float*, float*, int, int, cudaStream_t);
+template eig_status mirror_launch_column<float, uint16_t>(SpmmPlan*, const float*, float*, int, int, cudaStream_t);
+template eig_status mirror_launch_column<double, double>(SpmmPlan*, const double*, double*, int, int, cudaStream_t);
+template eig_status mirror_launch_column<double, float>(SpmmPlan*, const double*, double*, int, int, cudaStream_t);
+template eig_status mirror_launch_column<double, uint16_t>(SpmmPlan*, const double*, double*, int, int,
+                                                           cudaStream_t);
 
 }  // namespace eig

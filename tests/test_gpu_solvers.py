@@ -162,6 +162,57 @@ def test_block_lanczos_fp64(H3000):
     check_result(H, S, lam[:5])
 
 
+@pytest.mark.parametrize("vt", ["f32", "f64"])
+def test_decoupled_rmmdiis_equals_coupled(H3000f, vt):
+    """Decoupled RMM-DIIS (Sec. 4.3): once one wanted vector has converged, H r~ comes from one
+    SpMV per remaining vector.  Each SpMV sums its column in the block product's order, so the
+    iterates -- and the returned pairs -- are bitwise those of the coupled run, which the oracle
+    checks (test_hybrid_lobpcg_rmmdiis); only the products differ."""
+    H, lam = H3000f
+    X0 = guess(H, 8)
+    opts = dict(X0=X0, vec_type=vt, rmm_fallback=0, rmm_maxiter=500)
+    S = Solver(H, 5, 8)
+    rc0, st0 = S.solve("hybrid", **opts)
+    th0, X0r, rel0 = S.ritz()
+    rc1, st1 = S.solve("hybrid", rmm_decouple=1, **opts)
+    th1, X1r, rel1 = S.ritz()
+    S.close()
+    assert rc0 == rc1 == 0, (st0, st1)
+    assert st0["iterations_rmm"] == st1["iterations_rmm"] > 0
+    nb1 = 6 * (vt == "f64") + 0                      # shape index of the block-width-1 products
+    assert st0["spmm_calls_by_shape"][nb1] == 0 and st1["spmm_calls_by_shape"][nb1] > 0, st1
+    assert st1["spmm_calls"] > st0["spmm_calls"]
+    np.testing.assert_array_equal(th0, th1)
+    np.testing.assert_array_equal(X0r, X1r)
+    np.testing.assert_allclose(th1, lam[:5], rtol=1e-6)
+
+
+def test_block_lanczos_thick_restart_matches_oracle(H3000):
+    """Thick-restarted block Lanczos (Sec. 2.2): a basis of 4 blocks of 8, restarted from the 16
+    lowest Ritz vectors and the residual block, from a random start -- the dense eigenvalues, the
+    oracle's restarted iteration from the same start to within an iteration, and more iterations
+    than the basis holds blocks (so it restarted)."""
+    H, lam = H3000
+    X0 = random_block(H.n, 8, 11)
+    ref = O.block_lanczos(H, X0, 5, tol=1e-6, maxiter=400, restart=4, keep=16)
+    assert ref.converged and ref.extra["restarts"] >= 1
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("block_lanczos", X0=X0, vec_type="f64", lanczos_maxbasis=32, lanczos_keep=16, maxiter=400)
+    assert rc == 0, st
+    check_result(H, S, lam[:5])
+    assert st["iterations_front"] > 4
+    assert abs(st["iterations_front"] - ref.iterations) <= 2, (st["iterations_front"], ref.iterations)
+
+
+def test_block_lanczos_without_restart_stops_at_the_basis_limit(H3000):
+    H, lam = H3000
+    S = Solver(H, 5, 8)
+    rc, st = S.solve("block_lanczos", X0=random_block(H.n, 8, 11), vec_type="f64", lanczos_maxbasis=32,
+                     lanczos_keep=-1, maxiter=400)
+    from paper_2305_15552_gb300.binding import EIG_ENOT_CONVERGED
+    assert rc == EIG_ENOT_CONVERGED and st["iterations_front"] == 3, st
+
+
 def test_chebfsi_fp64(H3000):
     H, lam = H3000
     S = Solver(H, 5, 8)
