@@ -875,6 +875,10 @@ def run_sweep(args, ws, rank, local):
     is the optimum.  RMM-DIIS runs as printed (unpreconditioned, no LOBPCG safety net); a run that
     does not converge within 500 iterations is reported unconverged.  SpMV counts as Sec. 2.6
     counts them; times are single solves between CUDA events after one warm-up per method.
+    Also: block Lanczos alone with its thick restart (default), without restart and with a basis
+    of 8 blocks; for n_ev = 5, decoupled RMM-DIIS (one SpMV per remaining vector once c = 1..4
+    have converged, Sec. 4.3) against the coupled block product, with the time in products and
+    its "effective SpMV" count (that time over the time of one SpMV).
     `value` is the LOBPCG -> RMM-DIIS hybrid at tau <= 1e-7, n_ev = 5."""
     import torch
     torch.cuda.set_device(local)
@@ -894,7 +898,7 @@ def run_sweep(args, ws, rank, local):
             X0 = torch.tensor(initial_guess(H, a2, binding), device="cuda")
             S = binding.Solver(H, nev, nb)
             base = dict(vec_type="f64", tol=args.tol, maxiter=500, rmm_maxiter=500, rmm_fallback=0, rmm_precond=0,
-                        s_max=args.s_max, switch_res=0.0)
+                        s_max=args.s_max, switch_res=0.0, timing=1)
 
             def run(method, **o):
                 S.solve(method, X0=X0, **{**base, **o})
@@ -903,8 +907,13 @@ def run_sweep(args, ws, rank, local):
                 rc, st = S.solve(method, X0=X0, **{**base, **o})
                 e1.record()
                 torch.cuda.synchronize()
+                k1 = 6                                   # FP64 vectors, block width 1 (SpMV launches)
                 return {"converged": rc == 0, "spmv": int(st["spmv_count"]), "ms": e0.elapsed_time(e1),
-                        "front_iterations": st["iterations_front"], "rmm_iterations": st["iterations_rmm"]}
+                        "front_iterations": st["iterations_front"], "rmm_iterations": st["iterations_rmm"],
+                        "products_ms": float(sum(st["spmm_ms_by_shape"])),
+                        "spmv_launches": int(st["spmm_calls_by_shape"][k1]),
+                        "spmv_ms": float(st["spmm_ms_by_shape"][k1]),
+                        "block_launches": int(sum(st["spmm_calls_by_shape"]) - st["spmm_calls_by_shape"][k1])}
 
             rows = {}
             for front in ("lobpcg", "block_lanczos"):
@@ -923,6 +932,28 @@ def run_sweep(args, ws, rank, local):
                 rows[front] = fr
             for m in ("lanczos", "chebfilter", "rmmdiis"):
                 rows[m] = run(m)
+            # block Lanczos (f3): thick restart (the default, half the basis kept) against the old
+            # stop at the basis limit, and with a basis of only 8 blocks
+            rows["block_lanczos_no_restart"] = run("block_lanczos", switch_tau=0.0, lanczos_keep=-1)
+            rows["block_lanczos_basis8"] = dict(run("block_lanczos", switch_tau=0.0, lanczos_maxbasis=8 * nb),
+                                                basis_vectors=8 * nb)
+            if nev == 5:
+                # decoupled RMM-DIIS (f2, Sec. 4.3): after c = 1..4 converged vectors, one SpMV per
+                # remaining vector; c = 0 keeps the block product throughout.  "effective_spmv" is
+                # the time in products over the time of one SpMV (the paper divides by the
+                # SpMM/SpMV GFLOPS ratio instead)
+                dec = {}
+                for front in ("lobpcg", "block_lanczos"):
+                    for k in (5, 10, 15, 20):
+                        for cdec in range(5):
+                            dec[f"{front}_after_{k}_c{cdec}"] = run("hybrid", front=front, switch_after=k,
+                                                                    switch_tau=0.0, rmm_decouple=cdec)
+                per = [r["spmv_ms"] / r["spmv_launches"] for r in dec.values() if r["spmv_launches"]]
+                t1 = statistics.median(per) if per else None
+                for r in dec.values():
+                    r["effective_spmv"] = (r["products_ms"] / t1) if t1 else None
+                rows["decoupled_rmmdiis"] = dec
+                rows["spmv_ms"] = t1
             tables[f"nev{nev}_nb{nb}"] = rows
             if nev == 5:
                 value = rows["lobpcg"]["tau_1e-07"]["ms"]
