@@ -322,6 +322,10 @@ typedef struct {
   int64_t spmm_calls_by_shape[12];
   double spmm_ms_by_shape[12];
   double spmm_bytes_by_shape[12];
+  /* eig_solve_batch_ex with EIG_BATCH_LOCKSTEP: batched launches of the whole batch, and the  */
+  /* products they carried (the same values in every instance's stats); 0 otherwise           */
+  int64_t batch_launches;
+  int64_t batch_products;
 } eig_stats;
 
 /* Fills *o with the defaults documented in eig_opts. */
@@ -380,6 +384,23 @@ EIG_API eig_status eig_create_batch(const eig_csr_upper* Hs, int count, int n_ev
  * than EIG_OK / EIG_ENOT_CONVERGED / EIG_EDUPLICATE.  A handle must not appear twice. */
 EIG_API eig_status eig_solve_batch(void* const* handles, int count, eig_method method, const eig_opts* opts,
                                    int per_instance_opts, int threads, eig_status* status, eig_stats* stats);
+
+/* Flags of eig_solve_batch_ex. */
+#define EIG_BATCH_LOCKSTEP 1
+
+/* eig_solve_batch with flags.  EIG_BATCH_LOCKSTEP: the products of the running instances are
+ * launched together -- each instance's next SpMM (or fused Chebyshev step) waits until every
+ * running instance has posted its own, then one launch per product shape covers all of them,
+ * its CTAs the concatenated row blocks of the posted products (the (instance, row block) work
+ * list); an instance that has finished leaves the rounds (per-instance convergence).  Every
+ * other step of a solve still runs on its instance's stream.  Batched shapes: mirrored plans,
+ * FP32 values, block 8 or 16, FP32 or FP64 (double-float) vectors; other products of a round
+ * are launched one by one.  The results are bitwise those of eig_solve on each handle alone
+ * (each product sums in the single launch's order).  stats[i].batch_launches / batch_products
+ * count the batched launches and the products they carried. */
+EIG_API eig_status eig_solve_batch_ex(void* const* handles, int count, eig_method method, const eig_opts* opts,
+                                      int per_instance_opts, int threads, int flags, eig_status* status,
+                                      eig_stats* stats);
 
 typedef struct {
   int layout;       /* eig_layout */

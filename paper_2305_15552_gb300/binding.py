@@ -62,7 +62,8 @@ class Stats(C.Structure):
                 ("spmm_timed", C.c_int64), ("spmm_bytes", C.c_double), ("trace_rows", C.c_int),
                 ("iterations_fallback", C.c_int), ("precond_fallback", C.c_int), ("lp_spmm_calls", C.c_int64),
                 ("spmm_calls_by_shape", C.c_int64 * 12), ("spmm_ms_by_shape", C.c_double * 12),
-                ("spmm_bytes_by_shape", C.c_double * 12)]
+                ("spmm_bytes_by_shape", C.c_double * 12), ("batch_launches", C.c_int64),
+                ("batch_products", C.c_int64)]
 
 
 def stats_dict(stats):
@@ -114,6 +115,8 @@ _SIGS = {
                                     C.c_void_p]),
     "eig_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                   C.c_void_p]),
+    "eig_solve_batch_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                     C.c_void_p, C.c_void_p]),
     "eig_autotune_spmm": (C.c_int, [C.POINTER(CsrUpper), C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.POINTER(C.c_int), C.c_void_p]),
     "eig_lp_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
@@ -546,9 +549,10 @@ class TuneResult(C.Structure):
 LAYOUT_NAMES = {v: k for k, v in LAYOUTS.items()}
 
 
-def solve_batch(solvers, method="hybrid", X0s=None, opts=None, threads=0):
-    """eig_solve_batch over Solver objects; X0s: list (per instance) or None; opts: one dict for
+def solve_batch(solvers, method="hybrid", X0s=None, opts=None, threads=0, lockstep=False):
+    """eig_solve_batch_ex over Solver objects; X0s: list (per instance) or None; opts: one dict for
     all or a list of dicts.  Instances without a stream run on the batch's worker streams.
+    lockstep: the running instances' products are launched together (EIG_BATCH_LOCKSTEP).
     Returns (status of the batch, [status], [stats dict])."""
     lib = load()
     cnt = len(solvers)
@@ -565,8 +569,8 @@ def solve_batch(solvers, method="hybrid", X0s=None, opts=None, threads=0):
     stats = (Stats * max(cnt, 1))()
     import torch
     torch.cuda.synchronize()
-    rc = lib.eig_solve_batch(hs, cnt, METHODS[method] if isinstance(method, str) else int(method), arr,
-                             1 if per else 0, int(threads), st, stats)
+    rc = lib.eig_solve_batch_ex(hs, cnt, METHODS[method] if isinstance(method, str) else int(method), arr,
+                                1 if per else 0, int(threads), 1 if lockstep else 0, st, stats)
     del keeps
     out = [stats_dict(stats[i]) for i in range(cnt)]
     return rc, [int(st[i]) for i in range(cnt)], out

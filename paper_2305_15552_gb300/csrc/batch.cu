@@ -9,7 +9,12 @@
 // kernels and host round trips of different instances overlap.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -36,6 +41,90 @@ bool is_hard_error(eig_status s) {
 }
 
 }  // namespace
+
+// Lock-step products of a batch: every running instance's next SpMM (or fused Chebyshev step)
+// is posted here, and once all running instances have posted, the last poster launches the
+// round -- one launch per shape over the posted products' concatenated row blocks (the
+// (instance, row block) work list) on the batcher's stream, after every poster's stream has
+// reached its post (events), with every poster's stream ordered after the launch.  An
+// instance that finished (converged or stopped) no longer counts, so the work list of each
+// round holds exactly the running instances: the per-instance convergence mask.
+struct ProductBatcher {
+  struct Req {
+    SpmmJob job;
+    int nb;
+    eig_dtype vt;
+    bool cheb;
+    cudaEvent_t ready;
+    eig_status rc;
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  int running = 0;
+  uint64_t round = 0;
+  std::vector<Req> reqs;
+  std::vector<eig_status> results;    // of the last launched round, by post order
+  cudaStream_t ls = nullptr;
+  cudaEvent_t done = nullptr;
+  int64_t launches = 0, products = 0; // batched launches issued, products they carried
+
+  // all posted; called with mu held
+  void launch_round() {
+    results.assign(reqs.size(), EIG_OK);
+    for (auto& r : reqs) cudaStreamWaitEvent(ls, r.ready, 0);
+    std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+    for (int i = 0; i < (int)reqs.size(); ++i)
+      groups[std::make_tuple(reqs[i].nb, (int)reqs[i].vt, reqs[i].cheb ? 1 : 0)].push_back(i);
+    for (auto& g : groups) {
+      const int nb = std::get<0>(g.first);
+      const eig_dtype vt = (eig_dtype)std::get<1>(g.first);
+      const bool cheb = std::get<2>(g.first) != 0;
+      std::vector<SpmmJob> jobs;
+      for (int i : g.second) jobs.push_back(reqs[i].job);
+      eig_status s = spmm_run_batch(jobs.data(), (int)jobs.size(), nb, vt, cheb, ls);
+      if (s == EIG_OK) {
+        ++launches;
+        products += (int64_t)jobs.size();
+      } else if (s == EIG_EUNSUPPORTED) {
+        // shapes without a batched kernel: the products one by one, same stream, same order
+        s = EIG_OK;
+        for (int i : g.second) {
+          const SpmmJob& j = reqs[i].job;
+          eig_status t = cheb ? spmm_run_cheb(j.P, j.X, j.Y, nb, vt, j.Qp, j.active, j.alpha, j.c, j.first, ls)
+                              : spmm_run(j.P, j.X, j.Y, nb, vt, ls);
+          results[i] = t;
+        }
+      }
+      if (s != EIG_OK)
+        for (int i : g.second) results[i] = s;
+    }
+    cudaEventRecord(done, ls);
+    reqs.clear();
+    ++round;
+    cv.notify_all();
+  }
+};
+
+eig_status batch_product(ProductBatcher* b, Ctx& c, const SpmmJob& job, int nb, eig_dtype vt, bool cheb) {
+  if (!c.req_ev) EIG_CUDA_TRY(cudaEventCreateWithFlags(&c.req_ev, cudaEventDisableTiming));
+  EIG_CUDA_TRY(cudaEventRecord(c.req_ev, c.st));
+  std::unique_lock<std::mutex> lock(b->mu);
+  const size_t mine = b->reqs.size();
+  b->reqs.push_back({job, nb, vt, cheb, c.req_ev, EIG_OK});
+  const uint64_t r = b->round;
+  if ((int)b->reqs.size() >= b->running) {
+    b->launch_round();
+  } else if (!b->cv.wait_for(lock, std::chrono::seconds(120), [&] { return b->round != r; })) {
+    // an instance that neither posts nor leaves for two minutes (host work of that length)
+    // does not hold the others: the round goes out with the products posted so far
+    if (b->round == r) b->launch_round();
+  }
+  const eig_status rc = b->results[mine];
+  // ordered on this stream before any later round records `done` again: that round needs this
+  // instance's next post, which comes after this wait
+  cudaStreamWaitEvent(c.st, b->done, 0);
+  return rc;
+}
 }  // namespace eig
 
 using namespace eig;
@@ -58,31 +147,48 @@ eig_status eig_create_batch(const eig_csr_upper* Hs, int count, int n_ev, int bl
   return EIG_OK;
 }
 
-eig_status eig_solve_batch(void* const* handles, int count, eig_method method, const eig_opts* opts,
-                           int per_instance_opts, int threads, eig_status* status, eig_stats* stats) {
+eig_status eig_solve_batch_ex(void* const* handles, int count, eig_method method, const eig_opts* opts,
+                              int per_instance_opts, int threads, int flags, eig_status* status, eig_stats* stats) {
   if (count < 0 || (count > 0 && !handles)) return EIG_EINVAL;
   if (per_instance_opts && !opts) return EIG_EINVAL;
+  if (flags & ~EIG_BATCH_LOCKSTEP) return EIG_EINVAL;
   for (int i = 0; i < count; ++i)
     if (!handles[i]) return EIG_EINVAL;
   if (count == 0) return EIG_OK;
   int dev = 0;
   EIG_CUDA_TRY(cudaGetDevice(&dev));
   const int nt = std::max(1, std::min(count, threads > 0 ? threads : 16));
+  const bool lockstep = (flags & EIG_BATCH_LOCKSTEP) != 0;
+  ProductBatcher pb;
+  if (lockstep) {
+    EIG_CUDA_TRY(cudaStreamCreateWithFlags(&pb.ls, cudaStreamNonBlocking));
+    EIG_CUDA_TRY(cudaEventCreateWithFlags(&pb.done, cudaEventDisableTiming));
+    pb.running = nt;   // every worker's first instance; a worker leaves when the list is exhausted
+  }
+  auto leave = [&]() {
+    std::lock_guard<std::mutex> lock(pb.mu);
+    --pb.running;
+    if (!pb.reqs.empty() && (int)pb.reqs.size() >= pb.running) pb.launch_round();
+  };
   std::vector<eig_status> st(count, EIG_OK);
   std::vector<eig_stats> ss(count);
   std::atomic<int> next(0);
   std::atomic<int> setup_error(0);
   auto worker = [&]() {
-    if (cudaSetDevice(dev) != cudaSuccess) { setup_error = 1; return; }
     cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { setup_error = 1; return; }
+    if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      setup_error = 1;
+      if (lockstep) leave();
+      return;
+    }
     for (int i = next++; i < count; i = next++) {
       eig_opts o;
       if (!opts) eig_default_opts(&o);
       else o = per_instance_opts ? opts[i] : opts[0];
       if (!o.stream) o.stream = s;
-      st[i] = eig_solve(handles[i], method, &o, &ss[i]);
+      st[i] = solve_handle(handles[i], method, &o, &ss[i], lockstep ? &pb : nullptr);
     }
+    if (lockstep) leave();
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   };
@@ -90,14 +196,30 @@ eig_status eig_solve_batch(void* const* handles, int count, eig_method method, c
   pool.reserve(nt);
   for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
   for (auto& th : pool) th.join();
+  if (lockstep) {
+    cudaStreamSynchronize(pb.ls);
+    cudaEventDestroy(pb.done);
+    cudaStreamDestroy(pb.ls);
+  }
   if (setup_error) return EIG_ECUDA;
   eig_status first = EIG_OK;
   for (int i = 0; i < count; ++i) {
     if (status) status[i] = st[i];
-    if (stats) stats[i] = ss[i];
+    if (stats) {
+      stats[i] = ss[i];
+      if (lockstep) {
+        stats[i].batch_launches = pb.launches;
+        stats[i].batch_products = pb.products;
+      }
+    }
     if (first == EIG_OK && is_hard_error(st[i])) first = st[i];
   }
   return first;
+}
+
+eig_status eig_solve_batch(void* const* handles, int count, eig_method method, const eig_opts* opts,
+                           int per_instance_opts, int threads, eig_status* status, eig_stats* stats) {
+  return eig_solve_batch_ex(handles, count, method, opts, per_instance_opts, threads, 0, status, stats);
 }
 
 eig_status eig_autotune_spmm(const eig_csr_upper* H, int nb, eig_dtype vec_type, int reps, eig_tune_result* best,

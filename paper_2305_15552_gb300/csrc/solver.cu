@@ -182,6 +182,12 @@ void Ctx::count_spmm(int nb, eig_dtype vt, int64_t spmv_cols) {
 }
 
 eig_status Ctx::spmm(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols) {
+  if (batch) {
+    SpmmJob j{&h->plan, X, Y, nullptr, nullptr, 0.0, 0.0, 0};
+    EIG_TRY(batch_product(batch, *this, j, nb, vt, false));
+    count_spmm(nb, vt, spmv_cols);
+    return EIG_OK;
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   if (o.timing) {
     EIG_CUDA_TRY(cudaEventCreate(&a));
@@ -231,6 +237,13 @@ eig_status Ctx::rmm_product(const void* X, void* Y, int mp, eig_dtype vt, const 
 
 eig_status Ctx::spmm_cheb(const void* X, void* Y, int nb, eig_dtype vt, int64_t spmv_cols, const void* Qp,
                           const int* active, double alpha, double cshift, int first) {
+  if (batch) {
+    if (!h->plan.mirrored || (nb != 8 && nb != 16 && nb != 32)) return EIG_EUNSUPPORTED;
+    SpmmJob j{&h->plan, X, Y, Qp, active, alpha, cshift, first};
+    EIG_TRY(batch_product(batch, *this, j, nb, vt, true));
+    count_spmm(nb, vt, spmv_cols);
+    return EIG_OK;
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   if (o.timing) {
     EIG_CUDA_TRY(cudaEventCreate(&a));
@@ -256,6 +269,7 @@ Ctx::~Ctx() {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
+  if (req_ev) cudaEventDestroy(req_ev);
 }
 
 // Small-workspace carving
@@ -1421,6 +1435,14 @@ static eig_status solve_impl(Ctx& c, eig_method method) {
 }
 
 eig_status eig_solve(void* handle, eig_method method, const eig_opts* opts, eig_stats* stats) {
+  return solve_handle(handle, method, opts, stats, nullptr);
+}
+
+}  // extern "C"
+
+namespace eig {
+eig_status solve_handle(void* handle, eig_method method, const eig_opts* opts, eig_stats* stats,
+                        ProductBatcher* batch) {
   if (!handle) return EIG_EINVAL;
   eig_opts o;
   if (opts) o = *opts;
@@ -1437,11 +1459,15 @@ eig_status eig_solve(void* handle, eig_method method, const eig_opts* opts, eig_
   c.st = as_stream(o.stream);
   c.o = o;
   c.s = &local;
+  c.batch = batch;
   eig_status rc = solve_impl(c, method);
   cudaStreamSynchronize(c.st);
   if (stats) *stats = local;
   return rc;
 }
+}  // namespace eig
+
+extern "C" {
 
 eig_status eig_ritz(void* handle, double* theta, double* X, double* relres, int on_device) {
   if (!handle) return EIG_EINVAL;

@@ -45,12 +45,18 @@ struct Handle {
   DevBuf lp_buf[3], lp_small;
 };
 
+struct ProductBatcher;
+
 // Per-solve context
 struct Ctx {
   Handle* h;
   cudaStream_t st;
   eig_opts o;
   eig_stats* s;
+  // lock-step batches: every product goes through the batcher, which launches the products of
+  // all running instances together (batch.cu); req_ev orders this stream's work before it
+  ProductBatcher* batch = nullptr;
+  cudaEvent_t req_ev = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spmm_ev;
   std::vector<int> spmm_shape;   // product shape of each timed call (index of eig_stats' by-shape arrays)
   void count_spmm(int nb, eig_dtype vt, int64_t spmv_cols);
@@ -82,6 +88,14 @@ struct Ctx {
   }
   ~Ctx();
 };
+
+// The batcher's side of a product (batch.cu): posts job, waits for the round's launch, and
+// orders c.st after it.  EIG_EUNSUPPORTED for a Chebyshev step the plan cannot fuse (nothing
+// posted).
+eig_status batch_product(ProductBatcher* b, Ctx& c, const SpmmJob& job, int nb, eig_dtype vt, bool cheb);
+// Solve with an optional batcher (eig_solve: none).
+eig_status solve_handle(void* handle, eig_method method, const eig_opts* opts, eig_stats* stats,
+                        ProductBatcher* batch);
 
 // Stop rule of a front method: called after every iteration with the ascending Ritz values and
 // relative residuals of the leading `count` (>= n_ev) pairs; returns a switch reason (> 0) to stop.

@@ -509,6 +509,29 @@ static eig_status launch(SpmmPlan* P, const T* X, T* Y, T* Z, cudaStream_t st) {
   return transpose_reduce_launch<T, NB>(P, Z, Y, st);
 }
 
+template <typename T, typename V, int NB, bool CHEB>
+eig_status mirror_launch_batch(const SpmmJob* jobs, int count, cudaStream_t st);
+
+eig_status spmm_run_batch(const SpmmJob* jobs, int count, int nb, eig_dtype vt, bool cheb, cudaStream_t st) {
+  if (count < 1 || !jobs) return EIG_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!jobs[i].P || !jobs[i].P->mirrored || jobs[i].P->val_type != EIG_F32) return EIG_EUNSUPPORTED;
+  if (nb != 8 && nb != 16) return EIG_EUNSUPPORTED;
+  if (vt == EIG_F32) {
+    if (nb == 8) return cheb ? mirror_launch_batch<float, float, 8, true>(jobs, count, st)
+                             : mirror_launch_batch<float, float, 8, false>(jobs, count, st);
+    return cheb ? mirror_launch_batch<float, float, 16, true>(jobs, count, st)
+                : mirror_launch_batch<float, float, 16, false>(jobs, count, st);
+  }
+  if (vt == EIG_F64) {
+    if (nb == 8) return cheb ? mirror_launch_batch<double, float, 8, true>(jobs, count, st)
+                             : mirror_launch_batch<double, float, 8, false>(jobs, count, st);
+    return cheb ? mirror_launch_batch<double, float, 16, true>(jobs, count, st)
+                : mirror_launch_batch<double, float, 16, false>(jobs, count, st);
+  }
+  return EIG_EUNSUPPORTED;
+}
+
 template <typename T, typename V>
 eig_status mirror_launch_column(SpmmPlan* P, const T* X, T* Y, int ld, int col, cudaStream_t st);
 

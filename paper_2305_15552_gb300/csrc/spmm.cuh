@@ -84,6 +84,23 @@ size_t mirror_bytes_estimate(const SpmmPlan* P);
 // Builds the tile-contiguous copy (called by spmm_plan_build).
 eig_status spmm_plan_build_tiled(SpmmPlan* P, int cap, cudaStream_t st);
 eig_status spmm_run(SpmmPlan* P, const void* X, void* Y, int nb, eig_dtype vt, cudaStream_t st);
+// One product of a batched launch: Y = H X on plan P (cheb: the fused Chebyshev step
+// Y = alpha (H X - c X) - Qp, first = no Qp, X kept on inactive columns).
+struct SpmmJob {
+  SpmmPlan* P;
+  const void* X;
+  void* Y;
+  const void* Qp;
+  const int* active;
+  double alpha, c;
+  int first;
+};
+// Products of one shape -- block width nb, vector type vt, the plans' value type, plain or
+// Chebyshev -- in one launch over their concatenated row blocks (the (instance, row block)
+// work list of a batch); each product's sums are those of spmm_run / spmm_run_cheb.  Mirrored
+// plans with FP32 values and nb 8 or 16 (FP32 or FP64 vectors); EIG_EUNSUPPORTED otherwise,
+// with nothing launched.
+eig_status spmm_run_batch(const SpmmJob* jobs, int count, int nb, eig_dtype vt, bool cheb, cudaStream_t st);
 // Y(:, col) = H X(:, col) for blocks with row stride ld (one SpMV; mirrored layout only, else
 // EIG_EUNSUPPORTED).
 eig_status spmm_run_column(SpmmPlan* P, const void* X, void* Y, int ld, int col, eig_dtype vt, cudaStream_t st);

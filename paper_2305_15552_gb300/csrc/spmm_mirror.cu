@@ -473,6 +473,21 @@ struct MirrorEpi {
   int first;
 };
 
+// One product of a batched launch, and the batch (passed by value: at most kBatchJobs jobs).
+struct MirrorJob {
+  RsArgs a;
+  const void* X;
+  void* Y;
+  int ld, col0, xj_bulk;
+  MirrorEpi epi;
+};
+constexpr int kBatchJobs = 64;
+struct MirrorBatch {
+  int n;
+  int64_t cta0[kBatchJobs + 1];
+  MirrorJob jobs[kBatchJobs];
+};
+
 // Double-float accumulation applies to FP64 vectors with FP32 or BF16 values.
 template <typename T, typename V> struct MirrorDF { static constexpr bool value = false; };
 template <> struct MirrorDF<double, float> { static constexpr bool value = true; };
@@ -651,10 +666,11 @@ template <> struct Stage<double, true> {
   }
 };
 
-// Y (and X, Qp) rows have stride ld elements; this launch covers elements [col0, col0 + NB).
+// Row block I of one product.  Y (and X, Qp) rows have stride ld elements; the product covers
+// elements [col0, col0 + NB).
 template <typename T, typename V, int NB, bool CHEB>
-__global__ void __launch_bounds__(kW * 32, RsShape<T, V, NB>::MINB)
-k_spmm_mirror(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0, int xj_bulk, MirrorEpi epi) {
+__device__ __forceinline__ void mirror_row_block(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld,
+                                                 int col0, int xj_bulk, MirrorEpi epi, int64_t I) {
   typedef RsShape<T, V, NB> Sh;
   constexpr bool DF = Sh::DF;
   constexpr int RBY = Sh::RBY, LDB = Sh::LDB, NCH = Sh::NCH, EPC = Sh::EPC, PF = Sh::PF, VW = Sh::VW;
@@ -669,7 +685,6 @@ k_spmm_mirror(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld, int 
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t I = blockIdx.x;
   const int64_t r0 = I * kMR;
   const int p0 = a.rbp[I], p1 = a.rbp[I + 1];
 
@@ -841,6 +856,25 @@ k_spmm_mirror(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld, int 
   }
 }
 
+// One product: CTA = row block.
+template <typename T, typename V, int NB, bool CHEB>
+__global__ void __launch_bounds__(kW * 32, RsShape<T, V, NB>::MINB)
+k_spmm_mirror(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0, int xj_bulk, MirrorEpi epi) {
+  mirror_row_block<T, V, NB, CHEB>(a, X, Y, ld, col0, xj_bulk, epi, blockIdx.x);
+}
+
+// Several products of one shape in one launch over their concatenated row blocks (the
+// (instance, row block) work list of a batch): job j owns CTAs [cta0[j], cta0[j + 1]).
+template <typename T, typename V, int NB, bool CHEB>
+__global__ void __launch_bounds__(kW * 32, RsShape<T, V, NB>::MINB)
+k_spmm_mirror_batch(const __grid_constant__ MirrorBatch B) {
+  int j = 0;
+  while (j + 1 < B.n && B.cta0[j + 1] <= (int64_t)blockIdx.x) ++j;
+  const MirrorJob& J = B.jobs[j];
+  mirror_row_block<T, V, NB, CHEB>(J.a, static_cast<const T*>(J.X), static_cast<T*>(J.Y), J.ld, J.col0, J.xj_bulk,
+                                   J.epi, (int64_t)blockIdx.x - B.cta0[j]);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -910,14 +944,8 @@ template <typename T, typename V, int NB> struct RsSlice {
 };
 template <typename T, typename V> struct RsSlice<T, V, 1> { static constexpr int value = 1; };
 
-template <typename T, typename V, int NBK, bool CHEB>
-static eig_status rs_launch(SpmmPlan* P, const T* X, T* Y, int ld, int col0, const MirrorEpi& epi, cudaStream_t st) {
-  typedef RsShape<T, V, NBK> Sh;
-  int dev = 0, maxsm = 0;
-  EIG_CUDA_TRY(cudaGetDevice(&dev));
-  EIG_CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t sm = Sh::XBYTES + 16;
-  if (sm > (size_t)maxsm) return EIG_EUNSUPPORTED;
+// The plan's row streams as kernel arguments.
+static RsArgs rs_args(SpmmPlan* P) {
   RsArgs a;
   a.n = P->n;
   a.rbp = P->m_rbp.as<int32_t>();
@@ -930,8 +958,26 @@ static eig_status rs_launch(SpmmPlan* P, const T* X, T* Y, int ld, int col0, con
   a.bcol = P->m_bcol.as<uint16_t>();
   a.bval = P->m_bval.p;
   a.err = P->err.as<int>();
-  // X tiles by bulk copy: plain staging of whole, 16-byte aligned rows of a 16-byte multiple
-  const int xj_bulk = !Sh::DF && ld == NBK && (Sh::RBY % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
+  return a;
+}
+
+// X tiles by bulk copy: plain staging of whole, 16-byte aligned rows of a 16-byte multiple.
+template <typename T, typename V, int NBK>
+static int rs_xj_bulk(const T* X, int ld) {
+  typedef RsShape<T, V, NBK> Sh;
+  return !Sh::DF && ld == NBK && (Sh::RBY % 16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
+}
+
+template <typename T, typename V, int NBK, bool CHEB>
+static eig_status rs_launch(SpmmPlan* P, const T* X, T* Y, int ld, int col0, const MirrorEpi& epi, cudaStream_t st) {
+  typedef RsShape<T, V, NBK> Sh;
+  int dev = 0, maxsm = 0;
+  EIG_CUDA_TRY(cudaGetDevice(&dev));
+  EIG_CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t sm = Sh::XBYTES + 16;
+  if (sm > (size_t)maxsm) return EIG_EUNSUPPORTED;
+  const RsArgs a = rs_args(P);
+  const int xj_bulk = rs_xj_bulk<T, V, NBK>(X, ld);
   auto kern = k_spmm_mirror<T, V, NBK, CHEB>;
   EIG_CUDA_TRY(::eig::ensure_dyn_smem(kern, (int)sm));
   kern<<<(unsigned)P->nRB, kW * 32, sm, st>>>(a, X, Y, ld, col0, xj_bulk, epi);
@@ -945,6 +991,68 @@ eig_status mirror_launch(SpmmPlan* P, const T* X, T* Y, cudaStream_t st) {
   for (int c0 = 0; c0 < NB; c0 += NBK) EIG_TRY((rs_launch<T, V, NBK, false>(P, X, Y, NB, c0, MirrorEpi(), st)));
   return EIG_OK;
 }
+
+// Several products of one shape, each Y_i = H_i X_i (CHEB: the fused Chebyshev step with its
+// own Qp_i, active_i, alpha_i, c_i), in one launch per at most kBatchJobs column slices over
+// their concatenated row blocks; the sums are those of the single launch.
+template <typename T, typename V, int NB, bool CHEB>
+eig_status mirror_launch_batch(const SpmmJob* jobs, int count, cudaStream_t st) {
+  constexpr int NBK = RsSlice<T, V, NB>::value;
+  typedef RsShape<T, V, NBK> Sh;
+  int dev = 0, maxsm = 0;
+  EIG_CUDA_TRY(cudaGetDevice(&dev));
+  EIG_CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t sm = Sh::XBYTES + 16;
+  if (sm > (size_t)maxsm) return EIG_EUNSUPPORTED;
+  for (int i = 0; i < count; ++i)
+    if (!jobs[i].P->mirrored) return EIG_EUNSUPPORTED;
+  auto kern = k_spmm_mirror_batch<T, V, NBK, CHEB>;
+  EIG_CUDA_TRY(::eig::ensure_dyn_smem(kern, (int)sm));
+  MirrorBatch B;
+  B.n = 0;
+  int64_t ctas = 0;
+  auto flush = [&]() -> eig_status {
+    if (B.n == 0) return EIG_OK;
+    B.cta0[B.n] = ctas;
+    kern<<<(unsigned)ctas, kW * 32, sm, st>>>(B);
+    EIG_LAUNCH_CHECK(CHEB ? "k_spmm_mirror_batch_cheb" : "k_spmm_mirror_batch");
+    B.n = 0;
+    ctas = 0;
+    return EIG_OK;
+  };
+  for (int i = 0; i < count; ++i) {
+    const SpmmJob& q = jobs[i];
+    for (int c0 = 0; c0 < NB; c0 += NBK) {
+      MirrorJob& J = B.jobs[B.n];
+      J.a = rs_args(q.P);
+      J.X = q.X;
+      J.Y = q.Y;
+      J.ld = NB;
+      J.col0 = c0;
+      J.xj_bulk = rs_xj_bulk<T, V, NBK>(static_cast<const T*>(q.X), NB);
+      J.epi = MirrorEpi();
+      if (CHEB) {
+        J.epi.Qp = q.Qp;
+        J.epi.active = q.active;
+        J.epi.a = q.alpha;
+        J.epi.c = q.c;
+        J.epi.first = q.first;
+      }
+      B.cta0[B.n] = ctas;
+      ctas += q.P->nRB;
+      if (++B.n == kBatchJobs) EIG_TRY(flush());
+    }
+  }
+  return flush();
+}
+
+#define EIG_MIRROR_BATCH_INST(T, V)                                                                    \
+  template eig_status mirror_launch_batch<T, V, 8, false>(const SpmmJob*, int, cudaStream_t);           \
+  template eig_status mirror_launch_batch<T, V, 16, false>(const SpmmJob*, int, cudaStream_t);          \
+  template eig_status mirror_launch_batch<T, V, 8, true>(const SpmmJob*, int, cudaStream_t);            \
+  template eig_status mirror_launch_batch<T, V, 16, true>(const SpmmJob*, int, cudaStream_t);
+EIG_MIRROR_BATCH_INST(float, float)
+EIG_MIRROR_BATCH_INST(double, float)
 
 // One column of X (row stride ld, column col) times H into the same column of Y: the SpMV of
 // a decoupled RMM-DIIS vector (Sec. 4.3), summed in the order of the block product's column.

@@ -28,6 +28,35 @@ def instances():
 OPTS = dict(vec_type="f32", tol=1e-6, maxiter=500, switch_res=1e-3, switch_tau=0.0)
 
 
+@pytest.mark.parametrize("method,threads", [("hybrid", 6), ("hybrid", 2), ("chebfilter", 6)])
+def test_lockstep_batch_equals_single_solves(instances, method, threads):
+    """EIG_BATCH_LOCKSTEP: the running instances' products go out together, one launch per shape
+    over their concatenated row blocks.  Each product sums in the single launch's order, so every
+    instance returns bitwise what it returns alone; with fewer threads than instances, instances
+    join and leave the rounds as they start and finish."""
+    from paper_2305_15552_gb300.binding import Solver, solve_batch
+    Hs, X0s = instances
+    opts = dict(OPTS, cheb_degree=8) if method == "chebfilter" else OPTS
+    singles = []
+    for H, X0 in zip(Hs, X0s):
+        S = Solver(H, NEV, NB)
+        rc, st = S.solve(method, X0=X0, **opts)
+        singles.append((rc,) + tuple(S.ritz()))
+        S.close()
+    Ss = [Solver(H, NEV, NB) for H in Hs]
+    rc, sts, stats = solve_batch(Ss, method, X0s=X0s, opts=opts, threads=threads, lockstep=True)
+    assert rc == 0, sts
+    for i, S in enumerate(Ss):
+        th, X, rel = S.ritz()
+        rc1, th1, X1, rel1 = singles[i]
+        assert sts[i] == rc1
+        assert np.array_equal(th, th1) and np.array_equal(X, X1), f"instance {i} differs from its single solve"
+    launches, products = stats[0]["batch_launches"], stats[0]["batch_products"]
+    assert launches > 0 and products > launches, stats[0]   # rounds carried several instances
+    for S in Ss:
+        S.close()
+
+
 def test_batch_equals_single_solves_and_oracle(instances):
     from paper_2305_15552_gb300.binding import Solver, solve_batch
     Hs, X0s = instances
