@@ -482,7 +482,9 @@ def run_batch(args, ws, rank, local):
     n_ev = 5, block 8; each from its small-space start (computed beforehand, not timed).  Arms,
     each timed on the device over the whole batch: one instance after another on one stream;
     eig_solve_batch with worker streams; the same with each instance's SpMM plan shape chosen by
-    eig_autotune_spmm (tuning not timed).  Every rank runs the whole batch (replicas)."""
+    eig_autotune_spmm (tuning not timed); lock-step (EIG_BATCH_LOCKSTEP, one thread per instance:
+    each round's products of all running instances in one launch per shape).  Every rank runs the
+    whole batch (replicas)."""
     import torch
     torch.cuda.set_device(local)
     from paper_2305_15552_gb300 import binding
@@ -529,6 +531,10 @@ def run_batch(args, ws, rank, local):
                                                             threads=args.batch_threads))
         ms_tun, out_tun = timed(lambda: binding.solve_batch(S_tun, "hybrid", X0s=X0s, opts=opts,
                                                             threads=args.batch_threads))
+        ms_lock, out_lock = timed(lambda: binding.solve_batch(S_def, "hybrid", X0s=X0s, opts=opts,
+                                                              threads=args.batch_count, lockstep=True))
+    lock_stats = out_lock[2][0]
+    same_lock = all(sts_ == rc_ for sts_, (rc_, _) in zip(out_lock[1], out_seq))
     launches = lib.eig_launch_count() - launches0
     same = all(np.array_equal(a.ritz()[0], b.ritz()[0]) for a, b in zip(S_def, S_tun))
     conv_seq = sum(rc == 0 for rc, _ in out_seq)
@@ -556,6 +562,12 @@ def run_batch(args, ws, rank, local):
                    "threads": args.batch_threads, "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs mostly smaller than L2 individually, ~6 GB in total; no flush"},
         "sequential_ms": ms_seq, "batched_ms": ms_bat, "batched_tuned_ms": ms_tun,
+        "lockstep_ms": ms_lock,
+        "lockstep": {"what": "eig_solve_batch_ex with EIG_BATCH_LOCKSTEP, one thread per instance: each "
+                             "round's products of all running instances in one launch per shape over their "
+                             "concatenated row blocks", "batched_launches": int(lock_stats["batch_launches"]),
+                     "products_in_them": int(lock_stats["batch_products"]),
+                     "converged": int(sum(s_ == 0 for s_ in out_lock[1])), "statuses_equal_sequential": bool(same_lock)},
         "speedup_vs_sequential": ms_seq / ms_tun, "instances_per_s": args.batch_count / (ms_tun * 1e-3),
         "converged": {"sequential": conv_seq, "batched": conv_bat, "batched_tuned": conv_tun,
                       "of": args.batch_count},
@@ -573,10 +585,6 @@ SHAPE_NAMES = {0: "FP32 vectors, nb 1", 1: "FP32 vectors, nb 2", 2: "FP32 vector
                8: "FP64 vectors, nb 4", 9: "FP64 vectors, nb 8", 10: "FP64 vectors, nb 16",
                11: "FP64 vectors, nb 32"}
 
-# DRAM bytes per launch of the mirrored SpMM kernel (ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# one capture of the 500,000-row matrix of the same generator, ~400 nnz/row), per entry of the layout
-# (the layout streams every entry once per product, so traffic grows in proportion to the entries);
-# valid only for the kernel source whose SHA-256 prefix is `kernel_sha` (None after the kernel changed).
 # DRAM bytes per layout entry of k_spmm_mirror, from one ncu capture per shape at n = 500,000
 # (dram__bytes_read.sum + dram__bytes_write.sum over the plan's layout entries, 2.04e8); keyed
 # by the shape index 6 * (FP64 vectors) + log2(nb); void once spmm_mirror.cu changes.
