@@ -669,8 +669,8 @@ template <> struct Stage<double, true> {
 // Row block I of one product.  Y (and X, Qp) rows have stride ld elements; the product covers
 // elements [col0, col0 + NB).
 template <typename T, typename V, int NB, bool CHEB>
-__device__ __forceinline__ void mirror_row_block(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld,
-                                                 int col0, int xj_bulk, MirrorEpi epi, int64_t I) {
+__device__ __forceinline__ void mirror_row_block(const RsArgs& a, const T* __restrict__ X, T* __restrict__ Y, int ld,
+                                                 int col0, int xj_bulk, const MirrorEpi& epi, int64_t I) {
   typedef RsShape<T, V, NB> Sh;
   constexpr bool DF = Sh::DF;
   constexpr int RBY = Sh::RBY, LDB = Sh::LDB, NCH = Sh::NCH, EPC = Sh::EPC, PF = Sh::PF, VW = Sh::VW;
@@ -859,7 +859,8 @@ __device__ __forceinline__ void mirror_row_block(RsArgs a, const T* __restrict__
 // One product: CTA = row block.
 template <typename T, typename V, int NB, bool CHEB>
 __global__ void __launch_bounds__(kW * 32, RsShape<T, V, NB>::MINB)
-k_spmm_mirror(RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0, int xj_bulk, MirrorEpi epi) {
+k_spmm_mirror(const __grid_constant__ RsArgs a, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0,
+              int xj_bulk, const __grid_constant__ MirrorEpi epi) {
   mirror_row_block<T, V, NB, CHEB>(a, X, Y, ld, col0, xj_bulk, epi, blockIdx.x);
 }
 
