@@ -347,11 +347,12 @@ __device__ __forceinline__ float jacobi_den_f(double d, double th, float floor) 
   return den < 0.0f ? -mag : mag;
 }
 
-// Thread per (row, CPT adjacent columns); rows are read with 16-byte moves, the Rayleigh-Ritz
-// coefficients come from shared memory as CPT-wide vectors.  In place: the lanes of a row (one
-// warp) have read all their inputs before any of them writes (__syncwarp).
+// Thread per (row, CPT adjacent columns), three CTAs per SM (80 registers); rows are read with
+// 16-byte moves, the Rayleigh-Ritz coefficients come from shared memory as CPT-wide vectors.  In
+// place: the lanes of a row (one warp) have read all their inputs before any of them writes
+// (__syncwarp).
 template <typename T, int NB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_lobpcg_update(T* __restrict__ X, T* __restrict__ W, T* __restrict__ P, T* __restrict__ HX,
                 const T* __restrict__ HW, T* __restrict__ HP, const double* __restrict__ C, int k,
                 const double* __restrict__ theta, const double* __restrict__ diagH, double floor, int precond,

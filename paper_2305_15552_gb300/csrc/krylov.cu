@@ -122,8 +122,10 @@ __global__ void k_cheb(const T* __restrict__ HW, const T* __restrict__ W, const 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(i % k);
     if (!active[j]) { Y[i] = W[i]; continue; }
-    double y = a * ((double)HW[i] - c * (double)W[i]);
-    if (!first) y -= (double)Qp[i];
+    // explicit roundings (no contraction left to the compiler): the fused SpMM epilogue
+    // evaluates the same expression the same way, so both give the same bits
+    double y = __dmul_rn(a, __fma_rn(-c, (double)W[i], (double)HW[i]));
+    if (!first) y = __dsub_rn(y, (double)Qp[i]);
     Y[i] = (T)y;
   }
 }

@@ -835,8 +835,10 @@ __device__ __forceinline__ void mirror_row_block(const RsArgs& a, const T* __res
             if (!epi.active[jc0 + e]) {
               out.v[e] = xv.v[e];
             } else {
-              double yv = epi.a * ((double)(T)v[e] - epi.c * (double)xv.v[e]);
-              if (!epi.first) yv -= (double)qv.v[e];
+              // explicit roundings, as the separate elementwise step (k_cheb) takes them: the
+              // single and the batched launch then agree bit for bit
+              double yv = __dmul_rn(epi.a, __fma_rn(-epi.c, (double)xv.v[e], (double)(T)v[e]));
+              if (!epi.first) yv = __dsub_rn(yv, (double)qv.v[e]);
               out.v[e] = (T)yv;
             }
           }
