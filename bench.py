@@ -588,8 +588,8 @@ SHAPE_NAMES = {0: "FP32 vectors, nb 1", 1: "FP32 vectors, nb 2", 2: "FP32 vector
 # DRAM bytes per layout entry of k_spmm_mirror, from one ncu capture per shape at n = 500,000
 # (dram__bytes_read.sum + dram__bytes_write.sum over the plan's layout entries, 2.04e8); keyed
 # by the shape index 6 * (FP64 vectors) + log2(nb); void once spmm_mirror.cu changes.
-SPMM_TRAFFIC = {"kernel_sha": "ef3fca4f622a72cb", "per_layout_entry": {4: 1.311255e9 / 204360448, 3: 1.262595e9 / 204360448,
-                                                          9: 1.336279e9 / 204360448}}
+SPMM_TRAFFIC = {"kernel_sha": "b88641115d1ce339", "per_layout_entry": {4: 1.311198e9 / 204360448, 3: 1.262709e9 / 204360448,
+                                                          9: 1.336193e9 / 204360448}}
 
 
 def kernel_sha():

@@ -607,30 +607,50 @@ template <int N> struct RsAcc<double, N, false> {
 };
 // Double-float: X staged as (hi, lo) FP32 pairs (8 bytes per element, like FP64); each product
 // v * hi taken exactly (FMA two-product), summed into hi by two-sum, every error term and v * lo
-// into lo: ~2^-44 relative per step, at FP32 instruction rate.
+// into lo: ~2^-44 relative per step, at FP32 instruction rate.  A 16-byte piece holds two
+// elements as (hi_e, hi_e+1, lo_e, lo_e+1), so a step is FP32x2 arithmetic on element pairs;
+// every operation is an explicit round-to-nearest (a subtraction b - a is fma(a, -1, b)), so no
+// contraction can break the two-sum.  A one-element piece (block width 1) holds (hi, lo).
 template <int N> struct RsAcc<double, N, true> {
   typedef float VT;
   typedef double OT;
-  float hi[N], lo[N];
+  static constexpr int N2 = (N + 1) / 2;
+  float2 hi[N2], lo[N2];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int e = 0; e < N; ++e) hi[e] = lo[e] = 0.0f;
+    for (int e = 0; e < N2; ++e) hi[e] = lo[e] = make_float2(0.0f, 0.0f);
   }
   __device__ __forceinline__ void add(int slot0, float v, const uint32_t* w, int nw) {
-#pragma unroll
-    for (int e = 0; e < nw / 2; ++e) {
-      const int s = slot0 + e;
-      const float xh = __uint_as_float(w[2 * e]), xl = __uint_as_float(w[2 * e + 1]);
-      const float p = v * xh;
-      const float pe = fmaf(v, xh, -p);
-      const float t = hi[s] + p;
-      const float bb = t - hi[s];
-      const float err = (hi[s] - (t - bb)) + (p - bb);
+    if (nw == 4) {
+      const int s = slot0 / 2;
+      const float2 vv = make_float2(v, v), nv = make_float2(-v, -v), m1 = make_float2(-1.0f, -1.0f);
+      const float2 xh = make_float2(__uint_as_float(w[0]), __uint_as_float(w[1]));
+      const float2 xl = make_float2(__uint_as_float(w[2]), __uint_as_float(w[3]));
+      const float2 p = __fmul2_rn(vv, xh);
+      const float2 q = __ffma2_rn(nv, xh, p);                          // p - v hi: minus the product's error
+      const float2 t = __fadd2_rn(hi[s], p);
+      const float2 bb = __ffma2_rn(hi[s], m1, t);                      // t - hi
+      const float2 e1 = __ffma2_rn(__ffma2_rn(bb, m1, t), m1, hi[s]);  // hi - (t - bb)
+      const float2 e2 = __ffma2_rn(bb, m1, p);                         // p - bb
+      const float2 err = __fadd2_rn(e1, e2);
       hi[s] = t;
-      lo[s] = fmaf(v, xl, lo[s] + (err + pe));
+      lo[s] = __ffma2_rn(vv, xl, __fadd2_rn(lo[s], __ffma2_rn(q, m1, err)));
+    } else {
+      float& h = (slot0 & 1) ? hi[slot0 / 2].y : hi[slot0 / 2].x;
+      float& l = (slot0 & 1) ? lo[slot0 / 2].y : lo[slot0 / 2].x;
+      const float xh = __uint_as_float(w[0]), xl = __uint_as_float(w[1]);
+      const float p = __fmul_rn(v, xh);
+      const float pe = __fmaf_rn(v, xh, -p);
+      const float t = __fadd_rn(h, p);
+      const float bb = __fsub_rn(t, h);
+      const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+      h = t;
+      l = __fmaf_rn(v, xl, __fadd_rn(l, __fadd_rn(err, pe)));
     }
   }
-  __device__ __forceinline__ OT get(int e) const { return (double)hi[e] + (double)lo[e]; }
+  __device__ __forceinline__ OT get(int e) const {
+    return (e & 1) ? (double)hi[e / 2].y + (double)lo[e / 2].y : (double)hi[e / 2].x + (double)lo[e / 2].x;
+  }
 };
 
 // Value k (0..7) of a lane's streamed block, widened to the arithmetic type.
@@ -653,16 +673,25 @@ template <typename VT> struct BlkVal<double, VT> {
 // One staged X element of type T (FP32, FP64; double-float pairs are staged from FP64).
 template <typename T, bool DF> struct Stage;
 template <> struct Stage<float, false> {
-  __device__ __forceinline__ static void put(unsigned char* d, float x) { *reinterpret_cast<float*>(d) = x; }
+  __device__ __forceinline__ static void put(unsigned char* row, int e, int, float x) {
+    reinterpret_cast<float*>(row)[e] = x;
+  }
 };
 template <> struct Stage<double, false> {
-  __device__ __forceinline__ static void put(unsigned char* d, double x) { *reinterpret_cast<double*>(d) = x; }
+  __device__ __forceinline__ static void put(unsigned char* row, int e, int, double x) {
+    reinterpret_cast<double*>(row)[e] = x;
+  }
 };
 template <> struct Stage<double, true> {
-  __device__ __forceinline__ static void put(unsigned char* d, double x) {
+  // element e of a staged row: hi and lo words in the piece layout of the double-float
+  // accumulator (pairs of elements per 16-byte piece, or (hi, lo) for one-element rows)
+  __device__ __forceinline__ static void put(unsigned char* row, int e, int nb, double x) {
     const float h = __double2float_rn(x);
-    reinterpret_cast<float*>(d)[0] = h;
-    reinterpret_cast<float*>(d)[1] = __double2float_rn(x - (double)h);
+    float* d = reinterpret_cast<float*>(row);
+    const int ih = nb == 1 ? 0 : (e >> 1) * 4 + (e & 1);
+    const int il = nb == 1 ? 1 : ih + 2;
+    d[ih] = h;
+    d[il] = __double2float_rn(x - (double)h);
   }
 };
 
@@ -739,7 +768,7 @@ __device__ __forceinline__ void mirror_row_block(const RsArgs& a, const T* __res
         const int t = (int)(i / (kMC * NB));
         const int rr = (int)((i / NB) % kMC), e = (int)(i % NB);
         const int64_t row = (int64_t)a.tcol[t0 + t] * kMC + rr;
-        if (row < a.n) Stage<T, DF>::put(xs + (size_t)(t * kMC + rr) * RBY + (size_t)e * Sh::ES, X[row * ld + col0 + e]);
+        if (row < a.n) Stage<T, DF>::put(xs + (size_t)(t * kMC + rr) * RBY, e, NB, X[row * ld + col0 + e]);
       }
       __syncthreads();
     }
