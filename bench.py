@@ -588,8 +588,8 @@ SHAPE_NAMES = {0: "FP32 vectors, nb 1", 1: "FP32 vectors, nb 2", 2: "FP32 vector
 # DRAM bytes per layout entry of k_spmm_mirror, from one ncu capture per shape at n = 500,000
 # (dram__bytes_read.sum + dram__bytes_write.sum over the plan's layout entries, 2.04e8); keyed
 # by the shape index 6 * (FP64 vectors) + log2(nb); void once spmm_mirror.cu changes.
-SPMM_TRAFFIC = {"kernel_sha": "b88641115d1ce339", "per_layout_entry": {4: 1.311198e9 / 204360448, 3: 1.262709e9 / 204360448,
-                                                          9: 1.336193e9 / 204360448}}
+SPMM_TRAFFIC = {"kernel_sha": "ba31c0b68b1429a2", "per_layout_entry": {4: 1.310512e9 / 204360448, 3: 1.261945e9 / 204360448,
+                                                          9: 1.335326e9 / 204360448}}
 
 
 def kernel_sha():
@@ -707,7 +707,9 @@ def run_hybrid(args, ws, rank, local):
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
+        torch.cuda.nvtx.range_push("e2e_create")
         S2 = binding.Solver(Hp, args.nev, args.nb, layout=args.layout)
+        torch.cuda.nvtx.range_pop()
         S2.solve("hybrid", X0=X0p, vec_type=args.vec, tol=args.tol, maxiter=500, rmm_precond=args.rmm_precond,
                  switch_res=args.switch_res, switch_tau=args.switch_tau, switch_gap=args.switch_gap, s_max=args.s_max)
         S2.ritz(out=Xout)

@@ -51,6 +51,53 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// One row of a thread's TM x TM tile: its TM values of each block from shared memory (16-byte
+// loads where the tile is 16 bytes wide: rows are nb % TM == 0 elements, tiles TM-aligned, stages
+// 16-byte aligned), and the TM x TM products into the chunk sums, FP32 pairs by the FP32x2 FMA
+// (each element a single fused, round-to-nearest operation, as with fma).
+template <typename T, int TM> struct GramRow {
+  __device__ __forceinline__ static void load(const T* p, T* v) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i) v[i] = p[i];
+  }
+  __device__ __forceinline__ static void fma(const T* a, const T* b, T (*c)[TM]) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TM; ++j) c[i][j] = ::fma(a[i], b[j], c[i][j]);
+  }
+};
+template <> struct GramRow<float, 4> {
+  __device__ __forceinline__ static void load(const float* p, float* v) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  __device__ __forceinline__ static void fma(const float* a, const float* b, float (*c)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 ai = make_float2(a[i], a[i]);
+#pragma unroll
+      for (int j = 0; j < 4; j += 2) {
+        const float2 r = __ffma2_rn(ai, make_float2(b[j], b[j + 1]), make_float2(c[i][j], c[i][j + 1]));
+        c[i][j] = r.x;
+        c[i][j + 1] = r.y;
+      }
+    }
+  }
+};
+template <> struct GramRow<double, 4> {
+  __device__ __forceinline__ static void load(const double* p, double* v) {
+    const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  }
+  __device__ __forceinline__ static void fma(const double* a, const double* b, double (*c)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) c[i][j] = ::fma(a[i], b[j], c[i][j]);
+  }
+};
+
 // Thread t owns tiles t, t+256, ... of the (pair, ti, tj) grid of TM x TM tiles.  PIPE: the
 // chunks are staged by 16-byte cp.async copies into two shared-memory stages, the next chunk's
 // copies in flight while the current one is multiplied (rows of nb values must be a multiple of
@@ -121,12 +168,9 @@ k_gram(BlockList blocks, PairList pairs, int nb, int64_t n, int64_t rows_per_cta
         const T* Bb = sm + (size_t)pairs.b[q] * kGramRows * nb;
         for (int r = 0; r < kGramRows; ++r) {
           T av[TM], bv[TM];
-#pragma unroll
-          for (int i = 0; i < TM; ++i) { av[i] = Ab[r * nb + ti + i]; bv[i] = Bb[r * nb + tj + i]; }
-#pragma unroll
-          for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TM; ++j) cacc[s][i][j] = fma(av[i], bv[j], cacc[s][i][j]);
+          GramRow<T, TM>::load(Ab + r * nb + ti, av);
+          GramRow<T, TM>::load(Bb + r * nb + tj, bv);
+          GramRow<T, TM>::fma(av, bv, cacc[s]);
         }
 #pragma unroll
         for (int i = 0; i < TM; ++i)

@@ -166,15 +166,18 @@ __global__ void __launch_bounds__(kMR) k_mir_lower(int64_t n, const int64_t* __r
   }
 }
 
-// Upper part (diagonal included) after the lower part of each row.
+// Upper part (diagonal included) after the lower part of each row.  Warp per row: the lanes
+// copy consecutive entries.
 template <typename V>
 __global__ void k_mir_upper(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const V* __restrict__ val, const int64_t* __restrict__ lower,
                             const int64_t* __restrict__ fptr, int32_t* __restrict__ fcol, V* __restrict__ fval) {
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (r >= n) return;
-  const int64_t base = fptr[r] + lower[r] - rowptr[r];
-  for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+  const int64_t k0 = rowptr[r], k1 = rowptr[r + 1];
+  const int64_t base = fptr[r] + lower[r] - k0;
+  for (int64_t k = k0 + lane; k < k1; k += 32) {
     fcol[base + k] = col[k];
     fval[base + k] = val[k];
   }
@@ -255,23 +258,33 @@ __device__ __forceinline__ int pick_class(int want, const int* left) {
   return -1;
 }
 
-// Thread per (panel, slot): the slot's row's entries of the panel, class-ordered (the diagonal
-// entry last), into the lane's column of the warp's stream.
+// CTA per panel, thread per slot: the slot's row's entries of the panel, class-ordered (the
+// diagonal entry last), into the lane's column of the warp's stream.  The row's segment is read
+// in column order twice: once to count its entries per class, once to bucket their offsets by
+// class (each bucket in column order) into `sc` at the segment's own positions in the mirrored
+// CSR.  The class sequence is then chosen from the counts alone, and each streamed block's 8
+// steps (panel-local columns and values, padding after the row's last entry) are assembled in
+// registers and stored with 16-byte moves.  The tile of a column is looked up in the panel's
+// tile list, staged in shared memory.  Launch: blockDim.x == kMR, one block per panel.
 template <typename V>
-__global__ void k_rs_scatter(int64_t npan, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fcol,
-                             const V* __restrict__ fval, int64_t n, const int32_t* __restrict__ pan_rb,
-                             const int32_t* __restrict__ pt0, const int32_t* __restrict__ pnt,
-                             const int32_t* __restrict__ tcol, const uint8_t* __restrict__ perm,
-                             const int64_t* __restrict__ sboff, uint16_t* __restrict__ bcol, V* __restrict__ bval) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= npan * kMR) return;
-  const int64_t p = i / kMR;
-  const int slot = (int)(i % kMR), w = slot / kRW, lane = slot % kRW;
-  const int64_t r = (int64_t)pan_rb[p] * kMR + perm[i];
-  if (r >= n || pnt[p] == 0) return;
-  // the row's entries in this panel: columns in the panel's tile range
+__global__ void __launch_bounds__(kMR) k_rs_scatter(const int64_t* __restrict__ fptr, const int32_t* __restrict__ fcol,
+                                                    const V* __restrict__ fval, int64_t n,
+                                                    const int32_t* __restrict__ pan_rb, const int32_t* __restrict__ pt0,
+                                                    const int32_t* __restrict__ pnt, const int32_t* __restrict__ tcol,
+                                                    const uint8_t* __restrict__ perm, const int64_t* __restrict__ sboff,
+                                                    uint16_t* __restrict__ sc, uint16_t* __restrict__ bcol,
+                                                    V* __restrict__ bval) {
+  static_assert(kBS == 8 && (kBS * sizeof(V)) % 16 == 0, "a lane's block is whole 16-byte pieces");
+  __shared__ int32_t s_tc[kPT];
+  const int64_t p = blockIdx.x;
+  const int slot = threadIdx.x, w = slot / kRW, lane = slot % kRW;
   const int t0 = pt0[p], nt = pnt[p];
-  const int64_t first_cb = tcol[t0], last_cb = tcol[t0 + nt - 1];
+  if (slot < nt) s_tc[slot] = tcol[t0 + slot];
+  __syncthreads();
+  const int64_t r = (int64_t)pan_rb[p] * kMR + perm[p * kMR + slot];
+  if (r >= n || nt == 0) return;
+  // the row's entries in this panel: columns in the panel's tile range
+  const int64_t first_cb = s_tc[0], last_cb = s_tc[nt - 1];
   int64_t e0 = fptr[r], e1 = fptr[r + 1];
   {
     int64_t lo = e0, hi = e1;
@@ -287,39 +300,78 @@ __global__ void k_rs_scatter(int64_t npan, const int64_t* __restrict__ fptr, con
     }
     e1 = lo;
   }
-  // the diagonal entry, if it lies in this panel, takes the row's last step: the small
-  // off-diagonal terms are summed before the (typically much larger) diagonal one is added
-  int64_t ediag = -1;
-  for (int64_t e = e0; e < e1; ++e)
-    if ((int64_t)fcol[e] == r) ediag = e;
+  const int len = (int)(e1 - e0);  // at most kPT * kMC
+  // counts per class; the diagonal entry, if it lies in this panel, takes the row's last step:
+  // the small off-diagonal terms are summed before the (typically much larger) diagonal one
   int left[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int64_t cur[8];
-  for (int c = 0; c < 8; ++c) cur[c] = e0;
-  for (int64_t e = e0; e < e1; ++e)
-    if (e != ediag) left[fcol[e] & 7]++;
+  int ediag = -1;
+  for (int q = 0; q < len; ++q) {
+    const int32_t c = fcol[e0 + q];
+    if ((int64_t)c == r) ediag = q;
+    left[c & 7]++;
+  }
+  if (ediag >= 0) left[fcol[e0 + ediag] & 7]--;
+  // class buckets: offsets into the segment, column order within a class
+  int pos[8];
+  {
+    int run = 0;
+    for (int c = 0; c < 8; ++c) {
+      pos[c] = run;
+      run += left[c];
+    }
+  }
+  uint16_t* bucket = sc + e0;
+  {
+    int fill[8];
+    for (int c = 0; c < 8; ++c) fill[c] = pos[c];
+    for (int q = 0; q < len; ++q) {
+      if (q == ediag) continue;
+      const int c = fcol[e0 + q] & 7;
+      bucket[fill[c]++] = (uint16_t)q;
+    }
+  }
+  // the steps, a streamed block (8 steps of this lane) at a time
   const int64_t blk0 = sboff[p * kW + w];
-  const int64_t len = e1 - e0;
-  for (int64_t k = 0; k < len; ++k) {
-    int64_t e;
-    if (ediag >= 0 && k == len - 1) {
-      e = ediag;
-    } else {
-      const int c = pick_class((int)((lane + k) & 7), left);
-      e = cur[c];
-      while ((fcol[e] & 7) != c || e == ediag) ++e;
-      cur[c] = e + 1;
-      left[c]--;
+  for (int b = 0; b * kBS < len; ++b) {
+    uint32_t cw[kBS / 2] = {0u, 0u, 0u, 0u};
+    alignas(16) V vv[kBS];
+#pragma unroll
+    for (int j = 0; j < kBS; ++j) {
+      const int k = b * kBS + j;
+      uint32_t cc;
+      V v;
+      if (k < len) {
+        int q;
+        if (ediag >= 0 && k == len - 1) {
+          q = ediag;
+        } else {
+          const int c = pick_class((lane + k) & 7, left);
+          q = bucket[pos[c]++];
+          left[c]--;
+        }
+        const int64_t e = e0 + q;
+        const int32_t col = fcol[e];
+        const int32_t J = col / kMC;
+        int lo = 0, hi = nt - 1;  // position of J among the panel's tiles (ascending)
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (s_tc[mid] < J) lo = mid + 1; else hi = mid;
+        }
+        cc = (uint32_t)(lo * kMC + (col - J * kMC));
+        v = fval[e];
+      } else {  // padding, as k_rs_pads writes it
+        cc = (uint32_t)(kPR + ((lane + k) & 7));
+        v = V(0);
+      }
+      cw[j >> 1] |= cc << (16 * (j & 1));
+      vv[j] = v;
     }
-    const int32_t col = fcol[e];
-    const int32_t J = col / kMC;
-    int lo = 0, hi = nt - 1;  // position of J among the panel's tiles (ascending)
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (tcol[t0 + mid] < J) lo = mid + 1; else hi = mid;
-    }
-    const int64_t at = (blk0 + k / kBS) * kBE + lane * kBS + (k % kBS);
-    bcol[at] = (uint16_t)(lo * kMC + (col - J * kMC));
-    bval[at] = fval[e];
+    const int64_t at = (blk0 + b) * kBE + lane * kBS;
+    *reinterpret_cast<uint4*>(bcol + at) = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+    const uint4* src = reinterpret_cast<const uint4*>(vv);
+    uint4* dst = reinterpret_cast<uint4*>(bval + at);
+#pragma unroll
+    for (int u = 0; u < (int)(kBS * sizeof(V) / 16); ++u) dst[u] = src[u];
   }
 }
 
@@ -362,8 +414,8 @@ eig_status rowstream_fill(SpmmPlan* P, const int32_t* tile_rb, const int32_t* ti
                                                          fval.as<V>());
     EIG_LAUNCH_CHECK("k_mir_lower");
   }
-  k_mir_upper<V><<<(unsigned)gb, tb, 0, st>>>(n, P->rowptr, P->col, val, lower.as<int64_t>(), fptr.as<int64_t>(),
-                                              fcol.as<int32_t>(), fval.as<V>());
+  k_mir_upper<V><<<(unsigned)((n * 32 + tb - 1) / tb), tb, 0, st>>>(n, P->rowptr, P->col, val, lower.as<int64_t>(),
+                                                                    fptr.as<int64_t>(), fcol.as<int32_t>(), fval.as<V>());
   EIG_LAUNCH_CHECK("k_mir_upper");
   cnt.release();
   off.release();
@@ -437,11 +489,15 @@ eig_status rowstream_fill(SpmmPlan* P, const int32_t* tile_rb, const int32_t* ti
   EIG_TRY(P->m_bval.reserve(nent * sizeof(V)));
   k_rs_pads<V><<<(unsigned)((nent + tb - 1) / tb), tb, 0, st>>>(nent, P->m_bcol.as<uint16_t>(), P->m_bval.as<V>());
   EIG_LAUNCH_CHECK("k_rs_pads");
-  k_rs_scatter<V><<<(unsigned)((npan * kMR + tb - 1) / tb), tb, 0, st>>>(
-      npan, fptr.as<int64_t>(), fcol.as<int32_t>(), fval.as<V>(), n, d_pan_rb.as<int32_t>(), P->m_pt0.as<int32_t>(),
-      P->m_pnt.as<int32_t>(), P->m_tcol.as<int32_t>(), P->m_perm.as<uint8_t>(), P->m_sboff.as<int64_t>(),
-      P->m_bcol.as<uint16_t>(), P->m_bval.as<V>());
-  EIG_LAUNCH_CHECK("k_rs_scatter");
+  if (npan > 0) {
+    DevBuf sc;  // class buckets, at each row segment's positions in the mirrored CSR
+    EIG_TRY(sc.reserve(std::max<int64_t>(fnnz, 1) * 2));
+    k_rs_scatter<V><<<(unsigned)npan, kMR, 0, st>>>(
+        fptr.as<int64_t>(), fcol.as<int32_t>(), fval.as<V>(), n, d_pan_rb.as<int32_t>(), P->m_pt0.as<int32_t>(),
+        P->m_pnt.as<int32_t>(), P->m_tcol.as<int32_t>(), P->m_perm.as<uint8_t>(), P->m_sboff.as<int64_t>(),
+        sc.as<uint16_t>(), P->m_bcol.as<uint16_t>(), P->m_bval.as<V>());
+    EIG_LAUNCH_CHECK("k_rs_scatter");
+  }
   EIG_CUDA_TRY(cudaStreamSynchronize(st));  // temporaries go out of scope
   return EIG_OK;
 }
