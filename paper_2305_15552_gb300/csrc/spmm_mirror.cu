@@ -248,14 +248,33 @@ __global__ void k_rs_pads(int64_t nent, uint16_t* __restrict__ bcol, VS* __restr
 // Class (panel-local row mod 8) taken at a step whose lane wants class `want`: `want` while the
 // row has entries of it, else one that keeps its class mod 4, then mod 2.  Lane l wants
 // (l + step) mod 8, so the 8 lanes of a shared-memory phase read rows of 8 distinct classes.
-__device__ __forceinline__ int pick_class(int want, const int* left) {
+// `nz`: bit c set while the row has entries of class c left.
+__device__ __forceinline__ int pick_class(int want, unsigned nz) {
   const int order[8] = {0, 4, 2, 6, 1, 5, 3, 7};
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const int c = want ^ order[t];
-    if (left[c] > 0) return c;
+    if ((nz >> c) & 1u) return c;
   }
   return -1;
+}
+
+// Per-class counters held in registers: the 8 entries are only ever indexed by unrolled constant
+// indices (a run-time index would move the array to local memory).
+__device__ __forceinline__ int cls_get(const int (&a)[8], int c) {
+  int v = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v = (i == c) ? a[i] : v;
+  return v;
+}
+__device__ __forceinline__ void cls_add(int (&a)[8], int c, int d) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] += (i == c) ? d : 0;
+}
+__device__ __forceinline__ int cls_take(int (&a)[8], int c) {  // a[c]++
+  const int v = cls_get(a, c);
+  cls_add(a, c, 1);
+  return v;
 }
 
 // CTA per panel, thread per slot: the slot's row's entries of the panel, class-ordered (the
@@ -308,26 +327,29 @@ __global__ void __launch_bounds__(kMR) k_rs_scatter(const int64_t* __restrict__ 
   for (int q = 0; q < len; ++q) {
     const int32_t c = fcol[e0 + q];
     if ((int64_t)c == r) ediag = q;
-    left[c & 7]++;
+    cls_add(left, c & 7, 1);
   }
-  if (ediag >= 0) left[fcol[e0 + ediag] & 7]--;
+  if (ediag >= 0) cls_add(left, fcol[e0 + ediag] & 7, -1);
   // class buckets: offsets into the segment, column order within a class
   int pos[8];
+  unsigned nz = 0u;
   {
     int run = 0;
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
       pos[c] = run;
       run += left[c];
+      nz |= (left[c] > 0 ? 1u : 0u) << c;
     }
   }
   uint16_t* bucket = sc + e0;
   {
     int fill[8];
+#pragma unroll
     for (int c = 0; c < 8; ++c) fill[c] = pos[c];
     for (int q = 0; q < len; ++q) {
       if (q == ediag) continue;
-      const int c = fcol[e0 + q] & 7;
-      bucket[fill[c]++] = (uint16_t)q;
+      bucket[cls_take(fill, fcol[e0 + q] & 7)] = (uint16_t)q;
     }
   }
   // the steps, a streamed block (8 steps of this lane) at a time
@@ -345,9 +367,10 @@ __global__ void __launch_bounds__(kMR) k_rs_scatter(const int64_t* __restrict__ 
         if (ediag >= 0 && k == len - 1) {
           q = ediag;
         } else {
-          const int c = pick_class((lane + k) & 7, left);
-          q = bucket[pos[c]++];
-          left[c]--;
+          const int c = pick_class((lane + k) & 7, nz);
+          q = bucket[cls_take(pos, c)];
+          cls_add(left, c, -1);
+          if (cls_get(left, c) == 0) nz &= ~(1u << c);
         }
         const int64_t e = e0 + q;
         const int32_t col = fcol[e];
