@@ -588,8 +588,8 @@ SHAPE_NAMES = {0: "FP32 vectors, nb 1", 1: "FP32 vectors, nb 2", 2: "FP32 vector
 # DRAM bytes per layout entry of k_spmm_mirror, from one ncu capture per shape at n = 500,000
 # (dram__bytes_read.sum + dram__bytes_write.sum over the plan's layout entries, 2.04e8); keyed
 # by the shape index 6 * (FP64 vectors) + log2(nb); void once spmm_mirror.cu changes.
-SPMM_TRAFFIC = {"kernel_sha": "ba31c0b68b1429a2", "per_layout_entry": {4: 1.310512e9 / 204360448, 3: 1.261945e9 / 204360448,
-                                                          9: 1.335326e9 / 204360448}}
+SPMM_TRAFFIC = {"kernel_sha": "2628de426b5d0d6e", "per_layout_entry": {4: 1.310619e9 / 204360448, 3: 1.261674e9 / 204360448,
+                                                          9: 1.334987e9 / 204360448}}
 
 
 def kernel_sha():
