@@ -15,8 +15,9 @@ A step is one complete solve (eig_solve) with H resident in HBM.  The line also 
   * fp64_baseline: the same solve with FP64 values and vectors (the plain FP64 GPU solver);
   * e2e: the metric through the C ABI from host buffers (eig_create with H copied in and
     planned, eig_solve with a host X0, eig_ritz copying the eigenvectors back);
-  * cpu_baseline: the FP64 oracle's hybrid on a leading principal block of the same matrix on
-    all host cores, scaled by stored nonzeros (oracle_sample; --impl reference times the same).
+  * cpu_baseline: the FP64 oracle's hybrid solved on a smaller instance of the same workload
+    (same generator, density, block pattern and seed at n/40 rows) on all host cores, scaled by
+    stored nonzeros (oracle_sample; --impl reference times the same).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N] ...
   python bench.py --workload learned | batch | scale | sweep   (the other workloads)
