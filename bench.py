@@ -282,8 +282,8 @@ def cpu_baseline(H, args):
 
 
 def run_reference(args, ws, rank):
-    """--impl reference: the FP64 CPU oracle on this workload (the reference arm of this build is
-    the oracle).  Each step is one measured oracle_sample solve (ms_per_step is its wall time);
+    """--impl reference: the FP64 CPU oracle on this workload (the paper's method has no
+    published implementation to run, so the reference arm is the oracle).  Each step is one measured oracle_sample solve (ms_per_step is its wall time);
     `value` scales the median step to the bench matrix by stored nonzeros, as cpu_baseline does."""
     if rank != 0:
         return
